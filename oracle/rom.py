@@ -1,0 +1,210 @@
+"""Oracle rational Arnoldi model order reduction (TEST INFRASTRUCTURE ONLY).
+
+Follows the paper's Sec. 3.3 step by step:
+
+* projection basis: union over expansion points w_j of the Krylov subspaces
+  - second order (Eq. 9):  K(-Kt_j^-1 Dt_j, -Kt_j^-1 Mt_j; -Kt_j^-1 f_j) with
+    Kt_j = A(w_j), Dt_j = 2 i w_j M + D, Mt_j = M, built with the SOAR
+    recurrence of Bai and Su (2005), the paper's reference for Eq. 9;
+  - first order (Eq. 10) when there is no damping matrix (structural damping
+    enters as complex stiffness): K(-Kt_j^-1 M, -Kt_j^-1 f_j).
+  The shifted matrix Kt_j is factored once per expansion point and reused
+  for every moment of that point (Sec. 3.3, offline phase).
+  Moments are load specific: one starting vector per load column.
+* every new vector is orthonormalised against the basis by classical
+  Gram-Schmidt applied twice (CGS2), and dropped when its norm after the two
+  passes is below 1e-10 of its norm before them (deflation).
+* Galerkin projection (text after Eq. 11): [.]_R = V^H [.] V for K, D, M,
+  f_R = V^H f (the paper prints V^T f; for a complex V the Galerkin
+  projection needs V^H), y_R = C_R x_R with C_R = C^T V.
+* reduced sweep: dense GEPP of K_R + i w D_R - w^2 M_R at every frequency.
+* error measure eps(w) = |y - y_R| / |y| and eps_max = max_w eps(w)
+  (Sec. 3.3; the paper writes arg max, the value is what is tabulated).
+* greedy choice of expansion points (Sec. 3.3): the next point is the
+  candidate frequency with the largest estimated error; here the estimator
+  is the relative residual of the scaled full-order system.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import List, Optional
+
+import numpy as np
+
+from . import fom
+
+DEFLATION_TOL = 1e-10
+
+
+def cgs2_append(V: np.ndarray, W: np.ndarray, tol: float = DEFLATION_TOL):
+    """Append the columns of W to the orthonormal V, one at a time, by CGS2.
+
+    Returns (V_new, accepted) where ``accepted`` are the orthonormalised new columns.
+    """
+    cols = [V[:, i] for i in range(V.shape[1])]
+    new = []
+    for w in np.asarray(W).T:
+        w = w.astype(complex).copy()
+        pre = np.linalg.norm(w)
+        if pre == 0.0:
+            continue
+        for _ in range(2):
+            if cols:
+                Q = np.stack(cols, axis=1)
+                h = Q.conj().T @ w
+                w = w - Q @ h
+        nw = np.linalg.norm(w)
+        if nw <= tol * pre:
+            continue
+        q = w / nw
+        cols.append(q)
+        new.append(q)
+    Vn = np.stack(cols, axis=1) if cols else np.zeros((V.shape[0], 0), dtype=complex)
+    An = np.stack(new, axis=1) if new else np.zeros((V.shape[0], 0), dtype=complex)
+    return Vn, An
+
+
+def _first_order_moments(asm, lu, F, q):
+    """Moments of Eq. 10 at one expansion point: v_0 = Kt^-1 f, v_m = Kt^-1 M v_{m-1}."""
+    out = []
+    v = lu.solve(F)
+    out.append(v)
+    for _ in range(1, q):
+        v = lu.solve(asm.M @ v)
+        out.append(v)
+    return out
+
+
+def _soar(asm, lu, omega_j, f, q):
+    """SOAR (Bai and Su 2005) for the second-order Krylov space of Eq. 9.
+
+    A = -Kt^-1 Dt, B = -Kt^-1 M, starting vector u = -Kt^-1 f.  Returns an
+    orthonormal basis of span{r_0, ..., r_{q-1}} with r_1 = A r_0,
+    r_m = A r_{m-1} + B r_{m-2}.
+    """
+    Dt = 2j * omega_j * asm.M + asm.D
+    u = -lu.solve(f)
+    nu = np.linalg.norm(u)
+    Q = [u / nu]
+    P = [np.zeros_like(u)]
+    for j in range(q - 1):
+        r = -lu.solve(Dt @ Q[j] + asm.M @ P[j])
+        s = Q[j].copy()
+        for i in range(j + 1):
+            t = np.vdot(Q[i], r)
+            r = r - t * Q[i]
+            s = s - t * P[i]
+        t = np.linalg.norm(r)
+        if t <= DEFLATION_TOL * nu:
+            break
+        Q.append(r / t)
+        P.append(s / t)
+    return np.stack(Q, axis=1)
+
+
+def has_damping_matrix(asm) -> bool:
+    return asm.D.nnz > 0 and abs(asm.D).max() > 0.0
+
+
+def build_basis(asm, shifts_hz, q: int, F: np.ndarray, kmax: int, V0=None):
+    """Rational Arnoldi basis: union over the expansion points of Eq. 9 / Eq. 10 moments.
+
+    For each expansion point the shifted matrix is factored once; every load
+    column contributes q moments; each new vector is CGS2-orthonormalised
+    against everything accepted so far.  Stops at kmax columns.
+    """
+    V = np.zeros((asm.n, 0), dtype=complex) if V0 is None else V0
+    second = has_damping_matrix(asm)
+    for fj in shifts_hz:
+        om = 2.0 * np.pi * fj
+        lu = fom.BlockBandedLU(asm, om)
+        if second:
+            for c in range(F.shape[1]):
+                V, _ = cgs2_append(V, _soar(asm, lu, om, F[:, c], q))
+        else:
+            for blk in _first_order_moments(asm, lu, F, q):
+                V, _ = cgs2_append(V, blk)
+        if V.shape[1] >= kmax:
+            V = V[:, :kmax]
+            break
+    return V
+
+
+@dataclass
+class ReducedModel:
+    KR: np.ndarray
+    DR: np.ndarray
+    MR: np.ndarray
+    fR: np.ndarray
+    CR: np.ndarray
+
+    @property
+    def k(self) -> int:
+        return self.KR.shape[0]
+
+
+def project(asm, V: np.ndarray, F: np.ndarray, rcv_dofs) -> ReducedModel:
+    """Galerkin projection [.]_R = V^H [.] V, f_R = V^H f, C_R = C^T V (Sec. 3.3)."""
+    VH = V.conj().T
+    return ReducedModel(KR=VH @ (asm.K @ V), DR=VH @ (asm.D @ V), MR=VH @ (asm.M @ V),
+                        fR=VH @ F, CR=V[np.asarray(rcv_dofs)])
+
+
+def reduced_sweep(rm: ReducedModel, freqs_hz):
+    """y_R(w) = C_R (K_R + i w D_R - w^2 M_R)^-1 f_R at every frequency (Eq. 11)."""
+    out = np.empty((len(freqs_hz), rm.CR.shape[0], rm.fR.shape[1]), dtype=complex)
+    for i, f in enumerate(freqs_hz):
+        om = 2.0 * np.pi * f
+        AR = rm.KR + 1j * om * rm.DR - om ** 2 * rm.MR
+        out[i] = rm.CR @ np.linalg.solve(AR, rm.fR)
+    return out
+
+
+def relative_error(y: np.ndarray, yR: np.ndarray) -> np.ndarray:
+    """eps(w) = |y - y_R| / |y| elementwise (Sec. 3.3)."""
+    return np.abs(y - yR) / np.abs(y)
+
+
+def residual_estimate(asm, V, rm: ReducedModel, F, freqs_hz) -> np.ndarray:
+    """Relative residual ||R (F - A(w) V x_R)|| / ||R F|| of the scaled system, per frequency."""
+    out = np.empty(len(freqs_hz))
+    for i, f in enumerate(freqs_hz):
+        om = 2.0 * np.pi * f
+        AR = rm.KR + 1j * om * rm.DR - om ** 2 * rm.MR
+        xR = np.linalg.solve(AR, rm.fR)
+        r_s, _ = fom.equilibrate(asm, om)
+        res = r_s[:, None] * (F - asm.A(om) @ (V @ xR))
+        out[i] = np.linalg.norm(res) / np.linalg.norm(r_s[:, None] * F)
+    return out
+
+
+def greedy(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts: int,
+           initial_hz: Optional[List[float]] = None):
+    """Greedy expansion points: add the candidate with the largest residual estimate.
+
+    Ties go to the lowest frequency; candidates within one grid step of an
+    existing point are skipped.  Stops when the largest estimate is <= tol,
+    after max_shifts points, or at kmax columns.
+    """
+    cand_hz = np.asarray(cand_hz, dtype=float)
+    step = np.min(np.diff(cand_hz)) if len(cand_hz) > 1 else 0.0
+    shifts = list(initial_hz) if initial_hz else [float(cand_hz[len(cand_hz) // 2])]
+    V = build_basis(asm, shifts, q, F, kmax)
+    history = []
+    while True:
+        rm = project(asm, V, F, rcv_dofs)
+        est = residual_estimate(asm, V, rm, F, cand_hz)
+        history.append(float(est.max()))
+        if est.max() <= tol or len(shifts) >= max_shifts or V.shape[1] >= kmax:
+            break
+        order = np.argsort(-est, kind="stable")
+        nxt = None
+        for i in order:
+            if all(abs(cand_hz[i] - s) > step * 1.0001 for s in shifts):
+                nxt = float(cand_hz[i])
+                break
+        if nxt is None:
+            break
+        shifts.append(nxt)
+        V = build_basis(asm, [nxt], q, F, kmax, V0=V)
+    return shifts, V, project(asm, V, F, rcv_dofs), history

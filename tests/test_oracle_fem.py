@@ -1,0 +1,168 @@
+"""Pins for the oracle's FE assembly against closed forms and invariants.
+
+Paper: Sec. 2 (problem statement, Eq. 1-3), Eq. 5 (coupling matrix), Sec. 3.3
+(complex stiffness damping after Eq. 8).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+import workloads as W
+from oracle import fem
+
+
+def _fluid_block(asm, spec):
+    num = fem.Numbering(spec)
+    idx = np.array([num.p(i, j, k) for k in range(spec.nz) for j in range(spec.ny)
+                    for i in range(spec.nx)])
+    I, J, K = np.meshgrid(np.arange(spec.nx), np.arange(spec.ny), np.arange(spec.nz), indexing="ij")
+    I, J, K = (a.transpose(2, 1, 0).ravel() for a in (I, J, K))
+    Kf = asm.K[idx][:, idx].toarray().real
+    Mf = asm.M[idx][:, idx].toarray()
+    return Kf, Mf, I, J, K
+
+
+def _lam1d(l, N, h):
+    th = l * np.pi / (N - 1)
+    return 6.0 / h ** 2 * (1.0 - np.cos(th)) / (2.0 + np.cos(th))
+
+
+@pytest.mark.parametrize("lmn", [(1, 0, 0), (0, 2, 1), (2, 1, 3), (3, 3, 2)])
+def test_cavity_discrete_mode_exact(lmn):
+    """cos-modes sampled at the nodes are exact generalised eigenvectors of the
+    trilinear cavity with eigenvalue c^2 (lam_l + lam_m + lam_n)/c^2 (closed form)."""
+    w = W.small_model(nx=5, ny=4, nz=6, floor=False)
+    s = w.model
+    asm = fem.assemble(s)
+    Kf, Mf, I, J, K = _fluid_block(asm, s)
+    l, m, n = lmn
+    v = (np.cos(l * np.pi * I / (s.nx - 1)) * np.cos(m * np.pi * J / (s.ny - 1))
+         * np.cos(n * np.pi * K / (s.nz - 1)))
+    lam = (_lam1d(l, s.nx, s.Lx / (s.nx - 1)) + _lam1d(m, s.ny, s.Ly / (s.ny - 1))
+           + _lam1d(n, s.nz, s.Lz / (s.nz - 1)))
+    r = Kf @ v - lam * s.c ** 2 * (Mf @ v)
+    assert np.linalg.norm(r) <= 1e-13 * max(np.linalg.norm(Kf @ v), 1.0)
+
+
+def test_cavity_eigenfrequencies_converge_second_order():
+    """Lowest rigid-wall cavity modes converge to c/2 sqrt((l/Lx)^2+(m/Ly)^2+(n/Lz)^2) at O(h^2)."""
+    Lx, Ly, Lz, c = 0.6, 0.5, 1.0, 343.0
+    exact = sorted(c / 2 * np.sqrt((l / Lx) ** 2 + (m / Ly) ** 2 + (n / Lz) ** 2)
+                   for l in range(4) for m in range(4) for n in range(6))[1:6]
+    errs = []
+    for ref in (1, 2):
+        w = W.small_model(nx=3 * ref + 1, ny=3 * ref + 1, nz=5 * ref + 1, Lx=Lx, Ly=Ly, Lz=Lz,
+                          floor=False)
+        asm = fem.assemble(w.model)
+        Kf, Mf, *_ = _fluid_block(asm, w.model)
+        ev = la.eigh(Kf, Mf, eigvals_only=True)
+        f = np.sqrt(np.abs(ev[1:6])) / (2 * np.pi)
+        errs.append(np.max(np.abs(f - exact) / exact))
+    assert errs[1] < 0.06
+    assert errs[0] / errs[1] > 3.2          # second order: ~4x per halving of h
+
+
+def test_mass_and_coupling_sums():
+    """sum(Mf) = V/c^2; each wall coupling block sums to the lined wall area;
+    the floor damping sums to (rho/Z) * floor area; shell w-mass sums to rho_s t A."""
+    w = W.small_model(nx=5, ny=4, nz=6)
+    s = w.model
+    asm = fem.assemble(s)
+    fl = asm.is_fluid
+    V = s.Lx * s.Ly * s.Lz
+    assert np.isclose(asm.M[fl][:, fl].sum(), V / s.c ** 2, rtol=1e-13)
+    num = fem.Numbering(s)
+    wdofs = np.array([num.s(r, k, 0) for k in range(s.nz) for r in range(num.nr)])
+    inner = np.array([num.s(r, k, 0) for k in range(1, s.nz - 1) for r in range(num.nr)])
+    lateral = 2 * (s.Lx + s.Ly) * s.Lz
+    # -K_sf summed over all w rows = C summed = lateral area (before the end BC removes rows)
+    Csum_inner = -asm.K[inner][:, fl].sum().real
+    Mfs = asm.M[fl][:, wdofs].sum() / s.rho
+    hz = s.Lz / (s.nz - 1)
+    # the two end slabs lose their w rows to the simply supported edge; their area share
+    # is half an element height each
+    assert np.isclose(Csum_inner, lateral - 2 * (2 * (s.Lx + s.Ly)) * hz / 2, rtol=1e-12)
+    assert np.isclose(Mfs, lateral - 2 * (2 * (s.Lx + s.Ly)) * hz / 2, rtol=1e-12)
+    Dsum = asm.D.sum()
+    assert np.isclose(Dsum, s.rho / s.Z_floor * s.Lx * s.Lz, rtol=1e-12)
+    # shell translational mass restricted to the w DoFs of the inner slabs: full
+    # layers contribute rho_s t P hz, the two end layers rho_s t P hz/3 (one node of
+    # the 1-D consistent mass (hz/6)[[2,1],[1,2]]).
+    Mww = asm.M[inner][:, inner].sum()
+    P = 2 * (s.Lx + s.Ly)
+    assert np.isclose(Mww, s.rho_s * s.t * P * (s.Lz - 4 * hz / 3), rtol=1e-12)
+
+
+def test_hex_element_rigid_and_linear_patch():
+    """Ke annihilates constants; for a linear field the interior nodal flux vanishes."""
+    X = np.array([[0, 0, 0], [0.3, 0, 0], [0.3, 0.2, 0], [0, 0.2, 0],
+                  [0, 0, 0.4], [0.3, 0, 0.4], [0.3, 0.2, 0.4], [0, 0.2, 0.4]], dtype=float)
+    Ke, Me = fem.hex8_matrices(X)
+    assert np.abs(Ke @ np.ones(8)).max() < 1e-14
+    assert np.isclose(Me.sum(), 0.3 * 0.2 * 0.4, rtol=1e-14)
+    g = np.array([0.7, -1.3, 2.1])
+    u = X @ g
+    # energy of a linear field = |g|^2 * volume
+    assert np.isclose(u @ Ke @ u, g @ g * 0.3 * 0.2 * 0.4, rtol=1e-13)
+
+
+def _plate_ss_freqs(a, b, nex, ney, n_modes=4):
+    s = W.ModelSpec(Lx=1, Ly=1, Lz=1, nx=2, ny=2, nz=2)
+    K, M, xy = fem.plate_mesh(a, b, nex, ney, s.E, s.nu, s.rho_s, s.t)
+    on_edge = (np.isclose(xy[:, 0], 0) | np.isclose(xy[:, 0], a) | np.isclose(xy[:, 1], 0)
+               | np.isclose(xy[:, 1], b))
+    fixed = 3 * np.where(on_edge)[0]
+    free = np.setdiff1d(np.arange(K.shape[0]), fixed)
+    ev = la.eigh(K[np.ix_(free, free)].real, M[np.ix_(free, free)], eigvals_only=True,
+                 subset_by_index=[0, n_modes - 1])
+    return np.sqrt(ev) / (2 * np.pi), s
+
+
+def test_plate_simply_supported_modes_converge():
+    """Simply supported rectangular plate: f_mn -> (pi/2)((m/a)^2+(n/b)^2) sqrt(D/(rho t))
+    (Kirchhoff limit; t/a = 1/300 so transverse shear and rotary inertia are tiny)."""
+    a, b = 0.6, 0.45
+    errs = []
+    for ne in (16, 32):
+        f, s = _plate_ss_freqs(a, b, ne, int(ne * 3 / 4))
+        Dp = s.E * s.t ** 3 / (12 * (1 - s.nu ** 2))
+        exact = sorted(np.pi / 2 * ((m / a) ** 2 + (n / b) ** 2) * np.sqrt(Dp / (s.rho_s * s.t))
+                       for m in range(1, 5) for n in range(1, 5))[:4]
+        errs.append(np.max(np.abs(f - exact) / exact))
+    assert errs[1] < 0.01
+    assert errs[0] > 3.5 * errs[1]          # O(h^2): no shear locking at t/a = 1/300
+
+
+def test_developed_ring_plate_modes():
+    """The shell ring alone (periodic in s, simply supported ends) has modes
+    f = (1/2pi) sqrt(D/(rho t)) [(m pi/L)^2 + (2 pi n/P)^2] with P the perimeter."""
+    w = W.small_model(nx=9, ny=9, nz=13, Lx=0.5, Ly=0.5, Lz=0.8, floor=False, eta=0.0)
+    s = w.model
+    asm = fem.assemble(s)
+    sh = ~asm.is_fluid
+    num = fem.Numbering(s)
+    fixed = set(num.s(r, k, 0) for k in (0, s.nz - 1) for r in range(num.nr))
+    idx = np.array([i for i in np.where(sh)[0] if i not in fixed])
+    K = asm.K[idx][:, idx].toarray().real
+    M = asm.M[idx][:, idx].toarray()
+    ev = la.eigh(K, M, eigvals_only=True, subset_by_index=[0, 5])
+    f = np.sqrt(ev) / (2 * np.pi)
+    Dp = s.E * s.t ** 3 / (12 * (1 - s.nu ** 2))
+    P = 2 * (s.Lx + s.Ly)
+    ex = sorted(np.sqrt(Dp / (s.rho_s * s.t)) / (2 * np.pi) * ((m * np.pi / s.Lz) ** 2 +
+                (2 * np.pi * n / P) ** 2) for m in range(1, 4) for n in range(0, 4)
+                for _ in ((0,) if n == 0 else (0, 1)))[:6]
+    assert np.max(np.abs(f - ex) / ex) < 0.05
+
+
+def test_damping_enters_as_complex_stiffness():
+    """Shell stiffness carries (1 + i eta); the fluid block is real (Sec. 3.3)."""
+    w = W.small_model(eta=0.02, floor=False)
+    asm = fem.assemble(w.model)
+    sh = ~asm.is_fluid
+    Ks = asm.K[sh][:, sh].toarray()
+    ratio = Ks.imag[np.abs(Ks.real) > 1e-6 * np.abs(Ks.real).max()] / Ks.real[np.abs(Ks.real) > 1e-6 * np.abs(Ks.real).max()]
+    # every off-diagonal and non-BC diagonal entry has imag/real = eta
+    assert np.allclose(ratio[np.abs(ratio) > 0], 0.02, rtol=1e-12)
+    fl = asm.is_fluid
+    assert np.abs(asm.K[fl][:, fl].toarray().imag).max() == 0.0

@@ -1,0 +1,136 @@
+"""Pins for the oracle's rational Arnoldi ROM (Sec. 3.3, Eq. 9-11)."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fem, fom, rom
+
+
+def _setup(floor):
+    w = W.small_model(floor=floor)
+    asm = fem.assemble(w.model)
+    return w, asm, fem.load_matrix(w.model, w.loads, w.n_rhs), fem.receiver_dofs(w.model, w.receivers)
+
+
+def _span_gap(A, B):
+    """Largest sine of the principal angles between span(A) and span(B)."""
+    Qa, _ = np.linalg.qr(A)
+    Qb, _ = np.linalg.qr(B)
+    return float(np.linalg.norm(Qb - Qa @ (Qa.conj().T @ Qb), 2))
+
+
+def test_cgs2_orthonormal_and_deflates():
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((300, 20)) + 1j * rng.standard_normal((300, 20))
+    X[:, 7] = X[:, 2] * (1 + 1j) + 1e-13 * X[:, 3]     # numerically dependent column
+    V, acc = rom.cgs2_append(np.zeros((300, 0), complex), X)
+    assert V.shape[1] == 19
+    assert np.abs(V.conj().T @ V - np.eye(19)).max() < 1e-13
+    assert _span_gap(V, np.delete(X, 7, axis=1)) < 1e-10
+
+
+def test_first_order_basis_spans_explicit_moments():
+    """Eq. 10: span{Kt^-1 f, (Kt^-1 M) Kt^-1 f, ...} computed by explicit dense solves."""
+    w, asm, F, rc = _setup(floor=False)
+    fj = 140.0
+    V = rom.build_basis(asm, [fj], 4, F, 100)
+    A = asm.A(2 * np.pi * fj).toarray()
+    M = asm.M.toarray()
+    moments = []
+    v = np.linalg.solve(A, F)
+    for _ in range(4):
+        moments.append(v)
+        v = np.linalg.solve(A, M @ v)
+    Mm = np.hstack(moments)
+    # compare in a column-scaled basis (moment magnitudes grow geometrically)
+    Mm = Mm / np.linalg.norm(Mm, axis=0)
+    assert V.shape[1] == Mm.shape[1]
+    assert _span_gap(V, Mm) < 1e-6
+
+
+def test_soar_basis_spans_second_order_moments():
+    """Eq. 9: r_0 = Kt^-1 f, r_1 = A r_0, r_j = A r_{j-1} + B r_{j-2} with
+    A = -Kt^-1 (2 i w_j M + D), B = -Kt^-1 M."""
+    w, asm, F, rc = _setup(floor=True)
+    assert rom.has_damping_matrix(asm)
+    fj = 110.0
+    om = 2 * np.pi * fj
+    q = 4
+    V = rom.build_basis(asm, [fj], q, F[:, :1], 100)
+    Kt = asm.A(om).toarray()
+    Dt = (2j * om * asm.M + asm.D).toarray()
+    M = asm.M.toarray()
+    r = [np.linalg.solve(Kt, F[:, 0])]
+    r.append(-np.linalg.solve(Kt, Dt @ r[0]))
+    for j in range(2, q):
+        r.append(-np.linalg.solve(Kt, Dt @ r[j - 1]) - np.linalg.solve(Kt, M @ r[j - 2]))
+    R = np.stack([x / np.linalg.norm(x) for x in r], axis=1)
+    assert V.shape[1] == q
+    assert _span_gap(V, R) < 1e-6
+
+
+@pytest.mark.parametrize("floor", [False, True])
+def test_rom_interpolates_at_expansion_points(floor):
+    """The ROM reproduces the FOM output at every expansion point (moment matching of
+    order zero), up to the conditioning of the reduced system."""
+    w, asm, F, rc = _setup(floor)
+    shifts = [60.0, 150.0, 250.0]
+    V = rom.build_basis(asm, shifts, 3, F, 200)
+    rm = rom.project(asm, V, F, rc)
+    yR = rom.reduced_sweep(rm, shifts)
+    y, _ = fom.sweep(asm, shifts, F, rc, method="dense")
+    assert rom.relative_error(y, yR).max() < 1e-5
+    est = rom.residual_estimate(asm, V, rm, F, shifts)
+    assert est.max() < 1e-5
+
+
+def test_full_basis_reproduces_fom():
+    """With V spanning the whole space (k = n) the Galerkin ROM is the FOM."""
+    w = W.small_model(nx=3, ny=3, nz=4, Lx=0.3, Ly=0.3, Lz=0.4, floor=True, n_rcv=2)
+    asm = fem.assemble(w.model)
+    F = fem.load_matrix(w.model, w.loads, w.n_rhs)
+    rc = fem.receiver_dofs(w.model, w.receivers)
+    rng = np.random.default_rng(3)
+    V, _ = rom.cgs2_append(np.zeros((asm.n, 0), complex),
+                           rng.standard_normal((asm.n, asm.n)) + 0j)
+    assert V.shape[1] == asm.n
+    rm = rom.project(asm, V, F, rc)
+    yR = rom.reduced_sweep(rm, [80.0, 400.0])
+    y, _ = fom.sweep(asm, [80.0, 400.0], F, rc, method="dense")
+    # V unitary: A_R = V^H A V keeps the raw (unscaled) conditioning of A, ~1e11 here,
+    # so the forward check is loose; the backward error of V x_R (measured in the
+    # pressure/displacement-balanced norm of the full system) is the sharper one.
+    assert rom.relative_error(y, yR).max() < 1e-4
+    for f in (80.0, 400.0):
+        om = 2 * np.pi * f
+        AR = rm.KR + 1j * om * rm.DR - om ** 2 * rm.MR
+        x = V @ np.linalg.solve(AR, rm.fR)
+        assert fom.backward_error(asm, om, x, F) < 1e-8
+
+
+def test_galerkin_orthogonality():
+    """V^H (f - A(w) V x_R) = 0 at any frequency."""
+    w, asm, F, rc = _setup(floor=True)
+    V = rom.build_basis(asm, [70.0, 210.0], 3, F, 100)
+    rm = rom.project(asm, V, F, rc)
+    om = 2 * np.pi * 133.0
+    AR = rm.KR + 1j * om * rm.DR - om ** 2 * rm.MR
+    xR = np.linalg.solve(AR, rm.fR)
+    r = F - asm.A(om) @ (V @ xR)
+    assert np.linalg.norm(V.conj().T @ r) <= 1e-9 * np.linalg.norm(F)
+
+
+def test_greedy_picks_worst_candidate_and_improves():
+    w, asm, F, rc = _setup(floor=False)
+    cand = np.arange(40.0, 300.0, 10.0)
+    shifts, V, rm, hist = rom.greedy(asm, F, rc, cand, q=3, kmax=200, tol=1e-8, max_shifts=4,
+                                     initial_hz=[170.0])
+    assert len(shifts) == 4 and len(set(shifts)) == 4
+    # every chosen point is interpolated (the estimate collapses there)
+    est_at = rom.residual_estimate(asm, V, rm, F, shifts)
+    assert est_at.max() < 1e-5
+    # the second shift is the argmax of the first estimate away from the first point
+    V1 = rom.build_basis(asm, [170.0], 3, F, 200)
+    est = rom.residual_estimate(asm, V1, rom.project(asm, V1, F, rc), F, cand)
+    allowed = np.abs(cand - 170.0) > 10.0 * 1.0001
+    assert shifts[1] == cand[allowed][int(np.argmax(est[allowed]))]
