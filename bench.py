@@ -1,0 +1,306 @@
+"""Benchmark: full-order frequency-response sweep of the medium coupled model.
+
+Workload (the model the headline metric is quoted on): 1.5 x 1.5 x 6 m cavity
+at 24 x 24 x 96 nodes plus the shell ring, 81,792 DoF (b = 852 per slab, 96
+slabs), floor impedance, 4 seeded shell loads, 32 receivers, 481 frequencies
+20..500 Hz.  A step is one batch of `--batch` frequencies through the whole
+path: form A(w) -> block-banded LU in FP32 -> FP64 residual refinement to a
+relative residual of 1e-8 -> receivers and SPL.  value = frequencies / s over
+all ranks.  The factor store of one batch (~70 GB) is far larger than L2, so no
+separate L2 flush is needed between steps.
+
+--impl reference times the CPU oracle (oracle/, the plain FP64 restatement of
+the method) on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "FRF frequencies/sec at <=0.1 dB SPL error vs FP64 full-order sweep; tensor-pipe %"
+UNIT = "frequencies/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_reference(args):
+    """The oracle on the host cores, timed on a bounded sample of the workload."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    from oracle import fem, fom
+    w = W.config2()
+    asm = fem.assemble(w.model)
+    F = fem.load_matrix(w.model, w.loads, w.n_rhs)
+    rc = fem.receiver_dofs(w.model, w.receivers)
+    freqs = w.freqs_hz
+    sample = [freqs[(7 * i + 3) % len(freqs)] for i in range(max(1, args.warmup) + args.steps)]
+    times = []
+    for i, f in enumerate(sample):
+        t0 = time.perf_counter()
+        fom.sweep(asm, [f], F, rc, method="banded")
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+    per = sum(times) / len(times)
+    cores = os.cpu_count()
+    val = 1.0 / per
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "model_dofs": int(asm.n), "slab_block": int(asm.b), "slabs": int(asm.nz),
+                       "loads": w.n_rhs, "receivers": len(w.receivers), "step": "one frequency"},
+            "impl": "reference",
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} frequencies of the 481-point grid, block-banded GEPP FP64 "
+                                       f"(oracle.fom, numpy/scipy BLAS on {cores} host cores)"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sample(seconds_cap=40.0):
+    """Oracle frequencies/s on the host cores, one config-2 frequency (bounded sample)."""
+    from oracle import fem, fom
+    w = W.config2()
+    asm = fem.assemble(w.model)
+    F = fem.load_matrix(w.model, w.loads, w.n_rhs)
+    rc = fem.receiver_dofs(w.model, w.receivers)
+    t0 = time.perf_counter()
+    fom.sweep(asm, [233.0], F, rc, method="banded")
+    dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"1 frequency (233 Hz) of the config-2 sweep by the oracle's block-banded GEPP "
+                      f"in FP64, {dt:.1f} s"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--fp64-sample", type=int, default=2, help="frequencies timed on the plain FP64 path")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2310_04734_gb300 import api
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    w = W.config2()
+    spec = w.model
+    model = api.fsi_assemble(spec)
+    F = api.dense_loads(spec, w.loads, w.n_rhs)
+    rcv = torch.tensor(api.receiver_dofs(spec, w.receivers), device="cuda")
+    freqs = w.freqs_hz
+    B = args.batch
+    nsteps = args.warmup + args.steps
+
+    def batch_freqs(step):
+        # rank-sharded batches of the 481-point grid (wrapping); each rank sweeps its own frequencies
+        idx = (np.arange(B) + (step * world + rank) * B) % len(freqs)
+        return freqs[idx]
+
+    ws_bytes = api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers))
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    for s in range(args.warmup):
+        api.frf_sweep_full(model, batch_freqs(s), F, rcv, precision=args.precision, batch=B, max_refine=20,
+                           tol=1e-8, workspace=ws)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = np.zeros(8)
+    kern_flops = np.zeros(8)
+    kern_n = np.zeros(8, dtype=np.int64)
+    launches = 0
+    iters = []
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for s in range(args.warmup, nsteps):
+        r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, precision=args.precision, batch=B, max_refine=20,
+                               tol=1e-8, workspace=ws, profile=True)
+        kern_ms += np.array(r.stats.kernel_ms[:])
+        kern_flops += np.array(r.stats.kernel_flops[:])
+        kern_n += np.array(r.stats.kernel_launches[:])
+        launches += int(r.stats.launches)
+        iters.extend(r.iters.tolist())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    t_ms = ev0.elapsed_time(ev1)
+    if pg:
+        t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        t_ms = float(t.item())
+    total_freqs = args.steps * B * world
+    value = total_freqs / (t_ms / 1e3)
+
+    # end to end: same metric through the C ABI with host buffers (pinned), copies inside the call
+    e2e = None
+    if not args.no_e2e:
+        Fh = F.cpu().numpy()
+        Fpin = torch.from_numpy(np.asfortranarray(Fh).T.copy()).pin_memory()   # column-major bytes
+        Fview = Fpin.numpy().T
+        rh = rcv.cpu().numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ne = max(1, min(2, args.steps))
+        for s in range(ne):
+            api.frf_sweep_full(model, batch_freqs(nsteps + s), Fview, rh, precision=args.precision, batch=B,
+                               max_refine=20, tol=1e-8, host_io=True, workspace=ws)
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        h2d = Fh.size * 16 + rh.size * 4
+        d2h = B * rh.size * w.n_rhs * (16 + 8)
+        e2e = {"value": ne * B * world / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # plain FP64 full-order sweep on the same GPU (the metric's denominator), sampled
+    fp64 = None
+    if args.fp64_sample > 0:
+        fs = batch_freqs(0)[:args.fp64_sample]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r64 = api.frf_sweep_full(model, fs, F, rcv, precision="fp64", batch=len(fs), max_refine=1)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        rmix = api.frf_sweep_full(model, fs, F, rcv, precision=args.precision, batch=len(fs), max_refine=20,
+                                  tol=1e-8)
+        p64 = r64.p.cpu().numpy()
+        pm = rmix.p.cpu().numpy()
+        fp64 = {"value": len(fs) / t64, "unit": UNIT, "sample": f"{len(fs)} frequencies",
+                "max_spl_err_db_mixed_vs_fp64": float(np.max(np.abs(20 * np.log10(np.abs(pm) / np.abs(p64))))),
+                "max_rel_err_mixed_vs_fp64": float(np.max(np.abs(pm - p64) / np.abs(p64)))}
+
+    peaks, src = _peaks()
+    # dominant kernel: the FP32 complex GEMM update (SIMT FMA pipe); its peak is derived from
+    # 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    g = 0 if args.precision == "fp32_ir" else 0
+    achieved = kern_flops[g] / (kern_ms[g] / 1e3) / 1e12 if kern_ms[g] > 0 else None
+    roofline = {"bound": "alu", "kernel": "gemm_update_kernel<float2> (trailing complex GEMM of the band LU)",
+                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
+    shares = {k: {"ms": float(kern_ms[i]), "launches": int(kern_n[i]),
+                  "share": float(kern_ms[i] / max(kern_ms.sum(), 1e-9))}
+              for i, k in enumerate(["gemm", "panel", "trsm", "laswp", "form", "shift", "solve", "resid"])}
+
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline_sample()
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32 factor + f64 refinement" if args.precision == "fp32_ir" else "f64",
+                "data": "synthetic",
+                "config": {"workload": w.name, "model_dofs": int(model.dims.n), "slab_block": int(model.dims.b),
+                           "slabs": int(model.dims.nz), "loads": w.n_rhs, "receivers": len(w.receivers),
+                           "batch_frequencies": B, "refine_tol": 1e-8, "parallelism": f"replicas{world}",
+                           "l2": "inputs larger than L2 (factor store ~70 GB per batch)"},
+                "roofline": roofline, "kernels": shares, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clk, "fp64_full_order": fp64,
+                "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters))},
+                "peaks_source": src}
+        print(json.dumps(line), flush=True)
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

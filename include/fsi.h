@@ -1,0 +1,240 @@
+/*
+ * fsi.h -- C ABI of the GB300 frequency-response library for coupled
+ * shell-cavity (fluid-structure) finite-element models.
+ *
+ * The library computes the frequency sweep of the full-order model
+ *     A(w) x(w) = f,   A(w) = K + i w D - w^2 M,   y(w) = C^T x(w)
+ * (paper Sec. 2, Eq. 1-3, and Sec. 3.3, Eq. 8) on one GPU, and builds and
+ * evaluates rational Arnoldi reduced models of it (Sec. 3.3, Eq. 9-11).
+ *
+ * Conventions for every entry point
+ *   - Every function returns fsi_status: 0 on success, a negative code on
+ *     error.  No exception or abort crosses the ABI.  fsi_last_error() gives a
+ *     thread-local message for the last failure.
+ *   - Frequencies are in Hz, FP64, host memory.  w = 2 pi f.
+ *   - "device" pointers are CUDA global-memory pointers of the current device;
+ *     "host" pointers are ordinary CPU memory.  The caller allocates and owns
+ *     every buffer; the library allocates no device memory in these calls (the
+ *     workspace is the caller's).  Streams are borrowed (cudaStream_t as void*,
+ *     NULL = legacy default stream).  Calls are asynchronous on that stream
+ *     unless stated; any call that returns host-visible results synchronizes it.
+ *   - Complex numbers are fsi_c64 {re, im} pairs of doubles (complex128
+ *     layout).  Matrices are column-major unless stated: F[col * n + i].
+ *   - DoF numbering is slab major: slab k (nodes with z-index k) holds first the
+ *     nx*ny pressure DoFs, index i + nx*j, then (w, beta_s, beta_z) of every
+ *     shell ring node (ring numbered counter-clockwise from grid node (0, 0)).
+ *     Global index = k * b + local, b = nx*ny + 3*n_ring.
+ *   - On an error a sweep has completed and written every frequency batch
+ *     before the failing one (stats->n_done frequencies); nothing after it.
+ */
+#ifndef FSI_H
+#define FSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } fsi_c64;
+
+typedef enum {
+    FSI_OK = 0,
+    FSI_EINVAL = -1,      /* bad argument (sizes, pointers, options)                */
+    FSI_ENOMEM = -2,      /* workspace or model buffer smaller than required        */
+    FSI_ECUDA = -3,       /* a CUDA runtime call failed (message has the CUDA text) */
+    FSI_ESINGULAR = -4,   /* zero or non-finite pivot in a factorisation            */
+    FSI_ENOCONV = -5,     /* refinement did not reach the tolerance in max_refine   */
+    FSI_ETIMEOUT = -6,    /* a bounded device wait gave up                          */
+    FSI_ESTATE = -7       /* call out of order (e.g. reduced model not built)       */
+} fsi_status;
+
+typedef enum {
+    FSI_FP64 = 0,         /* factor and solve in FP64 (the plain full-order sweep)  */
+    FSI_FP32_IR = 1       /* factor in FP32, FP64 residual iterative refinement     */
+} fsi_precision;
+
+/* Geometry and materials of the coupled model (paper Sec. 2; loss factor
+ * Sec. 3.3 after Eq. 8).  All host memory; eta has n_eta = 1 (uniform) or
+ * nz - 1 (one per shell element layer between slabs k and k+1) entries. */
+typedef struct {
+    double Lx, Ly, Lz;            /* cavity box, m                                  */
+    int nx, ny, nz;               /* pressure nodes per direction (>= 3 each)       */
+    double c, rho;                /* air: speed of sound m/s, density kg/m^3        */
+    double E, nu, rho_s, t;       /* shell: Young's modulus, Poisson, density, m    */
+    const double* eta;            /* shell loss factor(s), host                      */
+    int n_eta;
+    int has_floor;                /* 1: locally reacting impedance on face y = 0   */
+    double Z_re, Z_im;            /* floor impedance, Pa s / m                       */
+} fsi_model_desc;
+
+/* Sizes derived from a description by fsi_model_dims. */
+typedef struct {
+    int64_t n;                    /* total DoFs = b * nz                           */
+    int b;                        /* DoFs per slab                                  */
+    int nz;                       /* slabs                                          */
+    int n_press_slab;             /* nx * ny                                        */
+    int n_ring;                   /* shell ring nodes per slab                      */
+    int64_t nnz;                  /* nonzeros of the shared CSR pattern of K, M, D */
+    size_t model_bytes;           /* size of the device model buffer                */
+    double rho;                   /* copied from the description                    */
+} fsi_dims;
+
+/* Compute sizes.  Host only, no CUDA call.  Errors: FSI_EINVAL. */
+fsi_status fsi_model_dims(const fsi_model_desc* desc, fsi_dims* out);
+
+/* Assemble K (complex), M (real), D (complex) on the host into caller-owned
+ * HOST arrays sharing one CSR pattern (paper Sec. 2, Eq. 1-3, coupling Eq. 5;
+ * D from the floor impedance, Eq. 8): rowptr[n+1], col[nnz] (sorted within
+ * each row), K[nnz], M[nnz], D[nnz].  No CUDA call.  Errors: FSI_EINVAL. */
+fsi_status fsi_assemble_host(const fsi_model_desc* desc, int32_t* rowptr, int32_t* col,
+                             fsi_c64* K, double* M, fsi_c64* D);
+
+/* Assemble and upload into a caller-allocated DEVICE buffer of at least
+ * dims.model_bytes bytes (256-byte aligned), on `stream`; synchronizes the
+ * stream before returning.  The buffer's layout is private to the library.
+ * Errors: FSI_EINVAL, FSI_ENOMEM (buffer too small), FSI_ECUDA. */
+fsi_status fsi_assemble(const fsi_model_desc* desc, void* d_model, size_t model_bytes,
+                        void* stream);
+
+typedef struct {
+    int precision;                /* fsi_precision                                   */
+    int batch;                    /* frequencies factored together (>= 1)            */
+    int max_refine;               /* refinement iterations cap (FP32_IR)             */
+    double tol;                   /* target relative residual in the scaled norm    */
+    int host_io;                  /* 1: F, rcv, p_out, spl_out are HOST pointers;   */
+                                  /*    the copies happen inside the call           */
+    int profile;                  /* 1: time every kernel launch with CUDA events   */
+                                  /*    on `stream` and report per-kernel totals    */
+} fsi_solve_opts;
+
+/* Kernel classes of the per-kernel totals in fsi_sweep_stats. */
+enum {
+    FSI_K_GEMM = 0,               /* trailing complex GEMM update of the band LU    */
+    FSI_K_PANEL = 1,              /* panel LU with partial pivoting                 */
+    FSI_K_TRSM = 2,               /* unit-lower triangular solve of pivot rows      */
+    FSI_K_LASWP = 3,              /* row interchanges                               */
+    FSI_K_FORM = 4,               /* dense scaled rows of A(w) from the CSR values  */
+    FSI_K_SHIFT = 5,              /* factor store write-out and window shift        */
+    FSI_K_SOLVE = 6,              /* forward / backward slab solves                 */
+    FSI_K_RESID = 7,              /* FP64 residual, refinement updates, receivers   */
+    FSI_K_COUNT = 8
+};
+
+typedef struct {
+    int n_done;                   /* frequencies completed                          */
+    int max_iters;                /* largest refinement count over frequencies      */
+    double max_relres;            /* largest final relative residual                */
+    int n_unconverged;            /* frequencies above tol after max_refine         */
+    int64_t launches;             /* kernel launches made by the call               */
+    /* with opts.profile: summed event time (ms), algorithmic real flops (complex  */
+    /* multiply-add = 8) and launch count per kernel class FSI_K_*                  */
+    double kernel_ms[8];
+    double kernel_flops[8];
+    int64_t kernel_launches[8];
+} fsi_sweep_stats;
+
+/* Workspace bytes needed by frf_sweep_full for these options.  Host only. */
+fsi_status frf_sweep_workspace(const fsi_dims* dims, const fsi_solve_opts* opts, int nrhs,
+                               int nrcv, size_t* bytes);
+
+/* Full-order frequency sweep (paper Sec. 2, Eq. 1; Sec. 3.3, Eq. 8): for every
+ * frequency solve A(w) X = F by a block-banded LU with partial pivoting across
+ * the stacked 2b x b panel of consecutive slabs, batched over `opts.batch`
+ * frequencies, then refine in FP64 (FSI_FP32_IR) and read the receivers.
+ *   d_model   device buffer filled by fsi_assemble
+ *   f_hz      host, nf frequencies
+ *   F         n x nrhs loads, column-major (device, or host if opts.host_io)
+ *   rcv       nrcv receiver DoF indices (device or host)
+ *   ws        device workspace of ws_bytes >= frf_sweep_workspace(...)
+ *   p_out     [nf][nrcv][nrhs] complex pressures (device or host)
+ *   spl_out   [nf][nrcv][nrhs] SPL, 20 log10(|p| / (sqrt(2) 20 uPa)), nullable
+ *   iters_out host [nf] refinement iterations per frequency, nullable
+ *   relres_out host [nf] final relative residual per frequency, nullable
+ *   stats     host, nullable
+ * Synchronizes the stream.  Errors: FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA,
+ * FSI_ESINGULAR, FSI_ENOCONV (results are still written). */
+fsi_status frf_sweep_full(const fsi_dims* dims, const void* d_model, const double* f_hz, int nf,
+                          const fsi_c64* F, int nrhs, const int32_t* rcv, int nrcv,
+                          const fsi_solve_opts* opts, void* ws, size_t ws_bytes,
+                          fsi_c64* p_out, double* spl_out, int32_t* iters_out,
+                          double* relres_out, fsi_sweep_stats* stats, void* stream);
+
+/* Residual R = F - A(w_f) X_f in FP64 for nf frequencies (the refinement's
+ * residual kernel, paper Eq. 8 operator).  Device arrays: X and R are
+ * [nf][nrhs][n] (for each frequency, column-major n x nrhs); F is n x nrhs.
+ * f_hz host.  Errors: FSI_EINVAL, FSI_ECUDA. */
+fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double* f_hz, int nf,
+                        const fsi_c64* X, const fsi_c64* F, int nrhs, fsi_c64* R, void* stream);
+
+/* Batched partial LU with partial pivoting (the factorisation kernel set used
+ * by every solve here), exposed for testing: for each of `batch` row-major
+ * matrices A_i (m x ncols, leading dimension ld >= ncols, stride sA elements
+ * between matrices) eliminate the first npiv columns, npiv <= min(m, ncols):
+ * afterwards rows 0..npiv-1 hold L\U of the pivot block and U's remaining
+ * columns, rows npiv..m-1 hold the multipliers (cols < npiv) and the Schur
+ * complement (cols >= npiv); ipiv[i*npiv + j] is the row swapped with row j
+ * (LAPACK getrf convention, 0-based).  precision selects FP64 or FP32 data:
+ * A points to fsi_c64 (FP64) or to {float re, im} pairs (FP32).  ws: device
+ * workspace of fsi_lu_workspace bytes.  status_out (host, nullable) gets the
+ * number of matrices that met a zero or non-finite pivot. */
+fsi_status fsi_lu_workspace(int batch, int m, size_t* bytes);
+fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, void* A, int64_t ld,
+                          int64_t sA, int32_t* ipiv, void* ws, size_t ws_bytes,
+                          int* n_singular_out, void* stream);
+
+typedef struct {
+    int precision;                /* factorisation per expansion point             */
+    int max_refine;               /* refinement cap per moment solve (FP32_IR)     */
+    double tol;                   /* refinement tolerance per moment solve         */
+    int second_order;             /* -1 auto (Eq. 9 if D != 0, else Eq. 10), 0, 1 */
+} fsi_rom_opts;
+
+/* Workspace bytes for rom_build. */
+fsi_status rom_workspace(const fsi_dims* dims, int nrhs, int q, int kmax, const fsi_rom_opts* opts,
+                         size_t* bytes);
+
+/* Rational Arnoldi basis (paper Sec. 3.3): for each expansion point w_j the
+ * shifted matrix Kt_j = A(w_j) is factored once (Sec. 3.3, offline phase) and
+ * q moments per load column are generated: Eq. 10 (first order,
+ * Kt_j^-1 M) when the model has no damping matrix, Eq. 9 (second order, SOAR
+ * recurrence with Dt_j = 2 i w_j M + D) otherwise.  Each new vector is
+ * orthonormalised against all accepted ones by two classical Gram-Schmidt
+ * passes (CGS2) and dropped if its norm falls below 1e-10 of its norm before
+ * them.  F: device n x nrhs.  V: device n x kmax column-major (output, first
+ * *k_out columns valid).  Errors: FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA,
+ * FSI_ESINGULAR. */
+fsi_status rom_build(const fsi_dims* dims, const void* d_model, const double* shifts_hz, int nshift,
+                     int q, const fsi_c64* F, int nrhs, int kmax, const fsi_rom_opts* opts,
+                     void* ws, size_t ws_bytes, fsi_c64* V, int* k_out, void* stream);
+
+/* Galerkin projection (text after Eq. 11): K_R = V^H K V, D_R = V^H D V,
+ * M_R = V^H M V (k x k), f_R = V^H F (k x nrhs), C_R = rows rcv of V
+ * (nrcv x k).  All device, column-major.  ws: device workspace of at least
+ * n * k * 16 bytes. */
+fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k,
+                       const fsi_c64* F, int nrhs, const int32_t* rcv, int nrcv, void* ws,
+                       size_t ws_bytes, fsi_c64* KR, fsi_c64* DR, fsi_c64* MR, fsi_c64* fR,
+                       fsi_c64* CR, void* stream);
+
+/* Workspace bytes for rom_sweep. */
+fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, size_t* bytes);
+
+/* Reduced sweep (Eq. 11): y_R(w) = C_R (K_R + i w D_R - w^2 M_R)^-1 f_R for nf
+ * frequencies, batched `batch` at a time, each reduced system equilibrated
+ * (row then column max scaling) and solved by dense LU with partial pivoting
+ * in FP64.  Inputs device (column-major), f_hz host; p_out [nf][nrcv][nrhs]
+ * device; spl_out same shape, nullable. */
+fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR,
+                     const fsi_c64* fR, const fsi_c64* CR, int nrhs, int nrcv,
+                     const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
+                     fsi_c64* p_out, double* spl_out, void* stream);
+
+const char* fsi_status_str(fsi_status s);
+const char* fsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSI_H */

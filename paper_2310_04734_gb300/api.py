@@ -1,0 +1,318 @@
+"""Python binding of the C ABI (include/fsi.h): argument marshalling only.
+
+Every step of the computation runs in libfsi.so's CUDA kernels.  PyTorch is
+used for device memory (caller-owned buffers) and the current CUDA stream.
+Function names follow the C entry points.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import _lib as L
+
+FSI_FP64 = 0
+FSI_FP32_IR = 1
+PRECISIONS = {"fp64": FSI_FP64, "fp32_ir": FSI_FP32_IR}
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None) -> C.c_void_p:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def _desc(spec):
+    """Marshal a workloads.ModelSpec into fsi_model_desc (keeps the eta array alive)."""
+    eta = np.ascontiguousarray(np.asarray(spec.eta, dtype=np.float64))
+    d = L.fsi_model_desc()
+    d.Lx, d.Ly, d.Lz = spec.Lx, spec.Ly, spec.Lz
+    d.nx, d.ny, d.nz = spec.nx, spec.ny, spec.nz
+    d.c, d.rho = spec.c, spec.rho
+    d.E, d.nu, d.rho_s, d.t = spec.E, spec.nu, spec.rho_s, spec.t
+    d.eta = eta.ctypes.data_as(L.c_double_p)
+    d.n_eta = int(eta.size)
+    if spec.Z_floor is not None:
+        d.has_floor = 1
+        d.Z_re, d.Z_im = float(np.real(spec.Z_floor)), float(np.imag(spec.Z_floor))
+    return d, eta
+
+
+def fsi_model_dims(spec) -> L.fsi_dims:
+    lib = L.load()
+    d, keep = _desc(spec)
+    out = L.fsi_dims()
+    L.check(lib.fsi_model_dims(C.byref(d), C.byref(out)), "fsi_model_dims")
+    return out
+
+
+def fsi_assemble_host(spec):
+    """Host CSR (rowptr, col, K, M, D) assembled by the library's C++ code."""
+    lib = L.load()
+    dims = fsi_model_dims(spec)
+    d, keep = _desc(spec)
+    rowptr = np.empty(dims.n + 1, np.int32)
+    col = np.empty(dims.nnz, np.int32)
+    K = np.empty(dims.nnz, np.complex128)
+    M = np.empty(dims.nnz, np.float64)
+    D = np.empty(dims.nnz, np.complex128)
+    L.check(lib.fsi_assemble_host(C.byref(d), rowptr.ctypes.data_as(L.c_int32_p),
+                                  col.ctypes.data_as(L.c_int32_p), C.c_void_p(K.ctypes.data),
+                                  M.ctypes.data_as(L.c_double_p), C.c_void_p(D.ctypes.data)),
+            "fsi_assemble_host")
+    return dims, rowptr, col, K, M, D
+
+
+@dataclass
+class DeviceModel:
+    spec: object
+    dims: L.fsi_dims
+    buf: object   # torch uint8 tensor on the device
+
+
+def fsi_assemble(spec, device="cuda") -> DeviceModel:
+    """Assemble on the host and upload into a torch-allocated device buffer."""
+    torch = _torch()
+    lib = L.load()
+    dims = fsi_model_dims(spec)
+    buf = torch.empty(int(dims.model_bytes) + 256, dtype=torch.uint8, device=device)
+    off = (-buf.data_ptr()) % 256
+    view = buf[off:off + int(dims.model_bytes)]
+    d, keep = _desc(spec)
+    L.check(lib.fsi_assemble(C.byref(d), _ptr(view), C.c_size_t(int(dims.model_bytes)), _stream_ptr()),
+            "fsi_assemble")
+    return DeviceModel(spec=spec, dims=dims, buf=view)
+
+
+def _opts(precision, batch, max_refine, tol, host_io, profile=False) -> L.fsi_solve_opts:
+    o = L.fsi_solve_opts()
+    o.profile = int(bool(profile))
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.batch = int(batch)
+    o.max_refine = int(max_refine)
+    o.tol = float(tol)
+    o.host_io = int(bool(host_io))
+    return o
+
+
+def frf_sweep_workspace(model: DeviceModel, precision="fp32_ir", batch=8, nrhs=1, nrcv=1,
+                        host_io=False) -> int:
+    lib = L.load()
+    o = _opts(precision, batch, 1, 1e-8, host_io)
+    nb = C.c_size_t()
+    L.check(lib.frf_sweep_workspace(C.byref(model.dims), C.byref(o), nrhs, nrcv, C.byref(nb)),
+            "frf_sweep_workspace")
+    return nb.value
+
+
+@dataclass
+class SweepResult:
+    p: object          # [nf][nrcv][nrhs] complex128 (torch on device, or numpy with host_io)
+    spl: object
+    iters: np.ndarray
+    relres: np.ndarray
+    stats: L.fsi_sweep_stats
+
+
+def frf_sweep_full(model: DeviceModel, freqs_hz: Sequence[float], F, rcv, precision="fp32_ir",
+                   batch=8, max_refine=10, tol=1e-8, host_io=False, workspace=None,
+                   allow_noconv=False, profile=False, outputs=None) -> SweepResult:
+    """Full-order sweep.  F: n x nrhs complex128 (torch CUDA tensor, or numpy with host_io);
+    rcv: receiver DoF indices (torch int32 CUDA tensor, or numpy with host_io)."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    if host_io:
+        Fh = np.asfortranarray(np.asarray(F, dtype=np.complex128))
+        nrhs = Fh.shape[1] if Fh.ndim == 2 else 1
+        Fbuf = Fh
+        Fp = C.c_void_p(Fh.ctypes.data)
+        rh = np.ascontiguousarray(np.asarray(rcv, dtype=np.int32))
+        nrcv = int(rh.size)
+        rp = C.c_void_p(rh.ctypes.data)
+        p = np.empty((nf, nrcv, nrhs), np.complex128)
+        spl = np.empty((nf, nrcv, nrhs), np.float64)
+        pp, sp = C.c_void_p(p.ctypes.data), C.c_void_p(spl.ctypes.data)
+    else:
+        nrhs = F.shape[1] if F.dim() == 2 else 1
+        Fbuf = F.t().contiguous() if F.dim() == 2 else F.contiguous()   # column-major n x nrhs
+        Fp = _ptr(Fbuf)
+        rbuf = rcv.to(torch.int32).contiguous()
+        nrcv = int(rbuf.numel())
+        rp = _ptr(rbuf)
+        p = torch.empty((nf, nrcv, nrhs), dtype=torch.complex128, device=F.device)
+        spl = torch.empty((nf, nrcv, nrhs), dtype=torch.float64, device=F.device)
+        pp, sp = _ptr(p), _ptr(spl)
+    o = _opts(precision, min(batch, nf), max_refine, tol, host_io, profile)
+    need = C.c_size_t()
+    L.check(lib.frf_sweep_workspace(C.byref(model.dims), C.byref(o), nrhs, nrcv, C.byref(need)),
+            "frf_sweep_workspace")
+    ws = workspace
+    if ws is None or ws.numel() < need.value:
+        ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    iters = np.zeros(nf, np.int32)
+    relres = np.zeros(nf, np.float64)
+    stats = L.fsi_sweep_stats()
+    st = lib.frf_sweep_full(C.byref(model.dims), _ptr(model.buf), f.ctypes.data_as(L.c_double_p), nf, Fp,
+                            nrhs, rp, nrcv, C.byref(o), _ptr(ws), C.c_size_t(ws.numel()), pp, sp,
+                            iters.ctypes.data_as(L.c_int32_p), relres.ctypes.data_as(L.c_double_p),
+                            C.byref(stats), _stream_ptr())
+    if not (allow_noconv and st == -5):
+        L.check(st, "frf_sweep_full")
+    return SweepResult(p=p, spl=spl, iters=iters, relres=relres, stats=stats)
+
+
+def fsi_residual(model: DeviceModel, freqs_hz, X, F):
+    """R_f = F - A(w_f) X_f (unscaled FP64).  X: [nf][n][nrhs] torch complex128, F: [n][nrhs]."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    Xc = X.transpose(1, 2).contiguous()          # [nf][nrhs][n]
+    Fc = F.t().contiguous()
+    R = torch.empty_like(Xc)
+    L.check(lib.fsi_residual(C.byref(model.dims), _ptr(model.buf), f.ctypes.data_as(L.c_double_p), nf,
+                             _ptr(Xc), _ptr(Fc), int(F.shape[1]), _ptr(R), _stream_ptr()), "fsi_residual")
+    return R.transpose(1, 2)
+
+
+def fsi_batched_lu(A, npiv: int):
+    """In-place batched partial LU of row-major A [batch][m][ncols] (complex64 or complex128 CUDA)."""
+    torch = _torch()
+    lib = L.load()
+    assert A.is_contiguous() and A.dim() == 3
+    batch, m, ncols = A.shape
+    prec = FSI_FP64 if A.dtype == torch.complex128 else FSI_FP32_IR
+    ipiv = torch.empty((batch, npiv), dtype=torch.int32, device=A.device)
+    need = C.c_size_t()
+    L.check(lib.fsi_lu_workspace(batch, m, C.byref(need)), "fsi_lu_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device=A.device)
+    nsing = C.c_int(0)
+    L.check(lib.fsi_batched_lu(prec, batch, m, ncols, npiv, _ptr(A), ncols, m * ncols, _ptr(ipiv), _ptr(ws),
+                               C.c_size_t(need.value), C.byref(nsing), _stream_ptr()), "fsi_batched_lu")
+    return ipiv, nsing.value
+
+
+def _rom_opts(precision="fp32_ir", max_refine=10, tol=1e-10, second_order=-1):
+    o = L.fsi_rom_opts()
+    o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    o.max_refine = int(max_refine)
+    o.tol = float(tol)
+    o.second_order = int(second_order)
+    return o
+
+
+def rom_build(model: DeviceModel, shifts_hz, q: int, F, kmax: int, precision="fp32_ir", max_refine=10,
+              tol=1e-10, second_order=-1):
+    """Rational Arnoldi basis V (n x k complex128, column-major as a [k][n] tensor transposed)."""
+    torch = _torch()
+    lib = L.load()
+    s = np.ascontiguousarray(np.asarray(shifts_hz, dtype=np.float64))
+    nrhs = F.shape[1]
+    o = _rom_opts(precision, max_refine, tol, second_order)
+    need = C.c_size_t()
+    L.check(lib.rom_workspace(C.byref(model.dims), nrhs, q, kmax, C.byref(o), C.byref(need)), "rom_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    Fc = F.t().contiguous()
+    Vt = torch.zeros((kmax, model.dims.n), dtype=torch.complex128, device="cuda")
+    k = C.c_int(0)
+    L.check(lib.rom_build(C.byref(model.dims), _ptr(model.buf), s.ctypes.data_as(L.c_double_p), int(s.size), q,
+                          _ptr(Fc), nrhs, kmax, C.byref(o), _ptr(ws), C.c_size_t(need.value), _ptr(Vt),
+                          C.byref(k), _stream_ptr()), "rom_build")
+    return Vt[:k.value].t()
+
+
+@dataclass
+class DeviceROM:
+    KR: object
+    DR: object
+    MR: object
+    fR: object
+    CR: object
+
+    @property
+    def k(self) -> int:
+        return int(self.KR.shape[0])
+
+
+def rom_project(model: DeviceModel, V, F, rcv) -> DeviceROM:
+    """Galerkin projection; V: n x k (torch, any layout), F: n x nrhs, rcv: int tensor."""
+    torch = _torch()
+    lib = L.load()
+    n, k = V.shape
+    nrhs = F.shape[1]
+    Vc = V.t().contiguous()          # column-major n x k
+    Fc = F.t().contiguous()
+    r = rcv.to(torch.int32).contiguous()
+    nrcv = int(r.numel())
+    ws = torch.empty(max(n * k * 16, 1) + 3 * 16 * k * k * 64, dtype=torch.uint8, device="cuda")
+    KR = torch.empty((k, k), dtype=torch.complex128, device="cuda")
+    DR = torch.empty_like(KR)
+    MR = torch.empty_like(KR)
+    fR = torch.empty((nrhs, k), dtype=torch.complex128, device="cuda")
+    CR = torch.empty((k, nrcv), dtype=torch.complex128, device="cuda")
+    L.check(lib.rom_project(C.byref(model.dims), _ptr(model.buf), _ptr(Vc), k, _ptr(Fc), nrhs, _ptr(r), nrcv,
+                            _ptr(ws), C.c_size_t(ws.numel()), _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR),
+                            _stream_ptr()), "rom_project")
+    # buffers are column-major: transpose views give the row-major matrices
+    return DeviceROM(KR=KR.t(), DR=DR.t(), MR=MR.t(), fR=fR.t(), CR=CR.t())
+
+
+def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256):
+    """Reduced sweep: receiver pressures [nf][nrcv][nrhs] and SPL (torch, device)."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    k = rom.k
+    nrhs = rom.fR.shape[1]
+    nrcv = rom.CR.shape[0]
+    cm = lambda X: X.t().contiguous()   # column-major buffers
+    KR, DR, MR, fR, CR = cm(rom.KR), cm(rom.DR), cm(rom.MR), cm(rom.fR), cm(rom.CR)
+    bt = min(batch, nf)
+    need = C.c_size_t()
+    L.check(lib.rom_sweep_workspace(k, nrhs, nrcv, bt, C.byref(need)), "rom_sweep_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    p = torch.empty((nf, nrcv, nrhs), dtype=torch.complex128, device="cuda")
+    spl = torch.empty((nf, nrcv, nrhs), dtype=torch.float64, device="cuda")
+    L.check(lib.rom_sweep(k, _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR), nrhs, nrcv,
+                          f.ctypes.data_as(L.c_double_p), nf, bt, _ptr(ws), C.c_size_t(need.value), _ptr(p),
+                          _ptr(spl), _stream_ptr()), "rom_sweep")
+    return p, spl
+
+
+def load_matrix_dofs(spec, loads, n_rhs):
+    """Load columns as (DoF index, column, value) triplets for the slab-major numbering."""
+    npl = spec.nx * spec.ny
+    b = npl + 3 * (2 * (spec.nx - 1) + 2 * (spec.ny - 1))
+    return [(ld.slab * b + npl + 3 * ld.ring, ld.column, ld.value) for ld in loads]
+
+
+def dense_loads(spec, loads, n_rhs, device="cuda"):
+    """n x nrhs complex128 load matrix on the device."""
+    torch = _torch()
+    npl = spec.nx * spec.ny
+    b = npl + 3 * (2 * (spec.nx - 1) + 2 * (spec.ny - 1))
+    F = torch.zeros((b * spec.nz, n_rhs), dtype=torch.complex128, device=device)
+    for g, c, v in load_matrix_dofs(spec, loads, n_rhs):
+        F[g, c] += complex(v)
+    return F
+
+
+def receiver_dofs(spec, receivers) -> np.ndarray:
+    npl = spec.nx * spec.ny
+    b = npl + 3 * (2 * (spec.nx - 1) + 2 * (spec.ny - 1))
+    return np.array([k * b + i + spec.nx * j for (i, j, k) in receivers], dtype=np.int32)

@@ -1,0 +1,55 @@
+// Host-side factor / solve engine shared by the full-order sweep and the ROM build.
+#pragma once
+
+#include <vector>
+
+#include "fsi_internal.h"
+#include "kernels.cuh"
+
+namespace fsi {
+
+DevModel dev_model(const fsi_dims& d, const void* blob);
+
+// ------------------------------------------------------------------ factor / solve engine
+// Per-batch buffers of one block-banded factorisation.
+template <typename R>
+struct Factor {
+    using T2 = typename Cplx<R>::T;
+    T2* G = nullptr;
+    T2* U = nullptr;
+    T2* L = nullptr;
+    int32_t* ipiv = nullptr;
+    int32_t* perm = nullptr;
+    int32_t* status = nullptr;
+    int64_t sG = 0, sU = 0, sL = 0, sP = 0, sPerm = 0;
+
+    void carve(Carver& c, const fsi_dims& d, int F) {
+        const int64_t b = d.b, nz = d.nz;
+        sG = 2 * b * 3 * b;
+        sU = nz * b * 3 * b;
+        sL = nz * b * b;
+        sP = nz * b;
+        sPerm = nz * 2 * b;
+        G = c.take<T2>(size_t(F) * sG);
+        U = c.take<T2>(size_t(F) * sU);
+        L = c.take<T2>(size_t(F) * sL);
+        ipiv = c.take<int32_t>(size_t(F) * sP);
+        perm = c.take<int32_t>(size_t(F) * sPerm);
+        status = c.take<int32_t>(size_t(F));
+    }
+};
+
+
+template <typename R>
+fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d_omega, cudaStream_t st);
+
+// Iterative refinement of A(w_f) x = B for every batch member: FP64 scaled
+// residual, correction by the stored factors in precision R.  On return xhat
+// holds the scaled solution (x = cs o xhat); it_done[f] is the first iteration
+// whose relative residual reached tol (-1: not reached), rel[f] the last one.
+template <typename R>
+fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev, int nrhs,
+                    double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms, int64_t sV,
+                    int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
+
+}  // namespace fsi

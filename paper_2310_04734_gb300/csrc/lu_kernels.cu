@@ -1,0 +1,721 @@
+// Batched dense kernels of the block-banded LU (paper Sec. 2: one direct solve
+// of A(w) per frequency step; here the slab-ordered matrix is factored as a
+// band whose pivot search spans the stacked panel of two consecutive slabs).
+//
+// Matrices are row-major complex (float2 / double2), batched over frequencies
+// with a fixed element stride.  The factorisation of one stacked window is a
+// right-looking partial LU over its first b columns:
+//   for each outer panel J (width NB):
+//     for each sub-panel j in J (width nbw, held in shared memory):
+//       panel LU with partial pivoting, row swaps inside the outer panel,
+//       unit-lower TRSM and a GEMM update restricted to the outer panel
+//     row swaps outside the outer panel, TRSM of the NB pivot rows, and the
+//     trailing GEMM update with K = NB.
+#include <cfloat>
+#include <cmath>
+
+#include "kernels.cuh"
+#include "prof.h"
+
+namespace fsi {
+
+namespace {
+
+constexpr int kPanelThreads = 1024;
+constexpr size_t kMaxPanelSmem = 220 * 1024;
+
+template <typename T2>
+struct Real;
+template <>
+struct Real<float2> {
+    using R = float;
+};
+template <>
+struct Real<double2> {
+    using R = double;
+};
+
+// ----------------------------------------------------------------- form rows
+template <typename T2>
+__global__ void form_rows_kernel(DevModel m, T2* G, int64_t sG, int ld, const double* omega, int row_slab,
+                                 int g_row0, int col_slab0, int wcols) {
+    using R = typename Real<T2>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (r >= m.b) return;
+    const int f = blockIdx.y;
+    const double w = omega[f];
+    const int64_t grow = int64_t(row_slab) * m.b + r;
+    T2* out = G + f * sG + int64_t(g_row0 + r) * ld;
+    for (int c = lane; c < wcols; c += 32) out[c] = mk<T2>(R(0), R(0));
+    __syncwarp();
+    const double rs = row_scale(m, grow, w);
+    const int64_t c0 = int64_t(col_slab0) * m.b;
+    const int e1 = m.rowptr[grow + 1];
+    for (int e = m.rowptr[grow] + lane; e < e1; e += 32) {
+        const int64_t col = m.col[e];
+        const int64_t lc = col - c0;
+        if (lc < 0 || lc >= wcols) continue;
+        const double2 a = a_entry(m, e, w);
+        const double s = rs * col_scale(m, col, w);
+        out[lc] = mk<T2>(R(a.x * s), R(a.y * s));
+    }
+}
+
+// ----------------------------------------------------------------- panel LU
+template <typename T2>
+__device__ void block_argmax(typename Real<T2>::R& val, int& idx, typename Real<T2>::R* sv, int* si) {
+    using R = typename Real<T2>::R;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int off = 16; off > 0; off >>= 1) {
+        R ov = __shfl_down_sync(0xffffffffu, val, off);
+        int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (ov > val || (ov == val && oi < idx)) {
+            val = ov;
+            idx = oi;
+        }
+    }
+    if (lane == 0) {
+        sv[warp] = val;
+        si[warp] = idx;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = blockDim.x >> 5;
+        val = lane < nw ? sv[lane] : R(-1);
+        idx = lane < nw ? si[lane] : 0x7fffffff;
+        for (int off = 16; off > 0; off >>= 1) {
+            R ov = __shfl_down_sync(0xffffffffu, val, off);
+            int oi = __shfl_down_sync(0xffffffffu, idx, off);
+            if (ov > val || (ov == val && oi < idx)) {
+                val = ov;
+                idx = oi;
+            }
+        }
+        if (lane == 0) {
+            sv[32] = val;
+            si[32] = idx;
+        }
+    }
+    __syncthreads();
+    val = sv[32];
+    idx = si[32];
+}
+
+// Panel rows [j0, m) x columns [j0, j0+nbw), column-major copy P[t * mr + i] in shared memory.
+template <typename T2>
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG, int ld, int m, int j0, int nbw,
+                                                              int32_t* ipiv, int64_t sP, int32_t* status) {
+    using R = typename Real<T2>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* sv = reinterpret_cast<R*>(smem_raw);
+    int* si = reinterpret_cast<int*>(smem_raw + 64 * sizeof(double));
+    T2* P = reinterpret_cast<T2*>(smem_raw + 64 * sizeof(double) + 64 * sizeof(int));
+    const int f = blockIdx.x;
+    T2* A = G + f * sG;
+    const int mr = m - j0;
+    for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
+        const int i = idx / nbw, t = idx - i * nbw;
+        P[t * mr + i] = A[int64_t(j0 + i) * ld + j0 + t];
+    }
+    __syncthreads();
+    for (int t = 0; t < nbw; ++t) {
+        R best = R(-1);
+        int bi = 0x7fffffff;
+        for (int i = t + threadIdx.x; i < mr; i += blockDim.x) {
+            const T2 v = P[t * mr + i];
+            const R a = v.x * v.x + v.y * v.y;
+            if (a > best || (a == best && i < bi)) {
+                best = a;
+                bi = i;
+            }
+        }
+        block_argmax<T2>(best, bi, sv, si);
+        const bool bad = !(best > R(0)) || isinf(best) || bi >= mr;
+        if (bad) {
+            if (threadIdx.x == 0) {
+                status[f] = 1;
+                ipiv[f * sP + j0 + t] = j0 + t;
+            }
+            __syncthreads();
+            continue;  // leave the column as is; the factor is singular
+        }
+        if (threadIdx.x == 0) ipiv[f * sP + j0 + t] = j0 + bi;
+        if (bi != t) {
+            for (int u = threadIdx.x; u < nbw; u += blockDim.x) {
+                const T2 x = P[u * mr + t];
+                P[u * mr + t] = P[u * mr + bi];
+                P[u * mr + bi] = x;
+            }
+        }
+        __syncthreads();
+        const T2 inv = cinv(P[t * mr + t]);
+        for (int i = t + 1 + threadIdx.x; i < mr; i += blockDim.x) {
+            const T2 l = cmul(P[t * mr + i], inv);
+            P[t * mr + i] = l;
+            for (int u = t + 1; u < nbw; ++u) cfms(P[u * mr + i], l, P[u * mr + t]);
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
+        const int i = idx / nbw, t = idx - i * nbw;
+        A[int64_t(j0 + i) * ld + j0 + t] = P[t * mr + i];
+    }
+}
+
+// ----------------------------------------------------------------- laswp
+template <typename T2>
+__global__ void laswp_kernel(T2* G, int64_t sG, int ld, int j, int cnt, const int32_t* ipiv, int64_t sP, int a0,
+                             int a1, int b0, int b1) {
+    const int f = blockIdx.y;
+    const int na = a1 > a0 ? a1 - a0 : 0;
+    const int nbc = b1 > b0 ? b1 - b0 : 0;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= na + nbc) return;
+    const int c = q < na ? a0 + q : b0 + (q - na);
+    T2* A = G + f * sG;
+    const int32_t* piv = ipiv + f * sP;
+    for (int t = 0; t < cnt; ++t) {
+        const int p = piv[j + t];
+        if (p != j + t) {
+            const T2 x = A[int64_t(j + t) * ld + c];
+            A[int64_t(j + t) * ld + c] = A[int64_t(p) * ld + c];
+            A[int64_t(p) * ld + c] = x;
+        }
+    }
+}
+
+// ----------------------------------------------------------------- trsm (unit lower)
+constexpr int kTrsmThreads = 128;
+template <typename T2>
+__global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(T2* G, int64_t sG, int ld, int j, int cnt, int c0,
+                                                            int c1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* Ls = reinterpret_cast<T2*>(smem_raw);     // cnt x cnt
+    T2* Bs = Ls + cnt * cnt;                      // cnt x kTrsmThreads
+    const int f = blockIdx.y;
+    T2* A = G + f * sG;
+    for (int idx = threadIdx.x; idx < cnt * cnt; idx += blockDim.x) {
+        const int r = idx / cnt, c = idx - r * cnt;
+        Ls[idx] = A[int64_t(j + r) * ld + j + c];
+    }
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = c < c1;
+    if (live)
+        for (int i = 0; i < cnt; ++i) Bs[i * kTrsmThreads + threadIdx.x] = A[int64_t(j + i) * ld + c];
+    __syncthreads();
+    if (!live) return;
+    for (int i = 1; i < cnt; ++i) {
+        T2 acc = Bs[i * kTrsmThreads + threadIdx.x];
+        for (int t = 0; t < i; ++t) cfms(acc, Ls[i * cnt + t], Bs[t * kTrsmThreads + threadIdx.x]);
+        Bs[i * kTrsmThreads + threadIdx.x] = acc;
+    }
+    for (int i = 1; i < cnt; ++i) A[int64_t(j + i) * ld + c] = Bs[i * kTrsmThreads + threadIdx.x];
+}
+
+// ----------------------------------------------------------------- gemm update
+// C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] * B[k0:k0+K, c0:c1] within one matrix of the batch.
+constexpr int kBM = 64, kBN = 64, kBK = 16, kGemmThreads = 256;
+template <typename T2>
+__global__ void __launch_bounds__(kGemmThreads) gemm_update_kernel(T2* G, int64_t sG, int ld, int r0, int r1,
+                                                                   int c0, int c1, int k0, int K) {
+    using R = typename Real<T2>::R;
+    __shared__ T2 As[kBK][kBM];
+    __shared__ T2 Bs[kBK][kBN];
+    const int f = blockIdx.z;
+    T2* A = G + f * sG;
+    const int rb = r0 + blockIdx.y * kBM, cb = c0 + blockIdx.x * kBN;
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    T2 acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = mk<T2>(R(0), R(0));
+    for (int kb = 0; kb < K; kb += kBK) {
+#pragma unroll
+        for (int q = 0; q < (kBM * kBK) / kGemmThreads; ++q) {
+            const int idx = tid + q * kGemmThreads;
+            const int r = idx / kBK, kk = idx - r * kBK;
+            const int gr = rb + r, gk = kb + kk;
+            As[kk][r] = (gr < r1 && gk < K) ? A[int64_t(gr) * ld + k0 + gk] : mk<T2>(R(0), R(0));
+        }
+#pragma unroll
+        for (int q = 0; q < (kBK * kBN) / kGemmThreads; ++q) {
+            const int idx = tid + q * kGemmThreads;
+            const int kk = idx / kBN, c = idx - kk * kBN;
+            const int gc = cb + c, gk = kb + kk;
+            Bs[kk][c] = (gc < c1 && gk < K) ? A[int64_t(k0 + gk) * ld + gc] : mk<T2>(R(0), R(0));
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            T2 a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b[q] = Bs[kk][tx + 16 * q];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) cfma(acc[i][q], a[i], b[q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gr = rb + ty + 16 * i;
+        if (gr >= r1) continue;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int gc = cb + tx + 16 * q;
+            if (gc >= c1) continue;
+            T2& c = A[int64_t(gr) * ld + gc];
+            c = csub(c, acc[i][q]);
+        }
+    }
+}
+
+// ----------------------------------------------------------------- slab shift
+template <typename T2>
+__global__ void slab_shift_kernel(T2* G, int64_t sG, int b, int m, T2* U, int64_t sU, T2* L, int64_t sL) {
+    using R = typename Real<T2>::R;
+    const int f = blockIdx.y;
+    const int ld = 3 * b;
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= int64_t(b) * ld) return;
+    const int r = int(q / ld), c = int(q - int64_t(r) * ld);
+    T2* A = G + f * sG;
+    U[f * sU + q] = A[q];
+    const bool two = (m == 2 * b);
+    if (two && c < b) L[f * sL + int64_t(r) * b + c] = A[int64_t(b + r) * ld + c];
+    A[q] = (two && c < 2 * b) ? A[int64_t(b + r) * ld + b + c] : mk<T2>(R(0), R(0));
+}
+
+__global__ void perm_kernel(const int32_t* ipiv, int64_t sP, int32_t* perm, int64_t sPerm, int b, int m) {
+    extern __shared__ int32_t sperm[];
+    const int f = blockIdx.x;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) sperm[i] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int32_t* piv = ipiv + f * sP;
+        for (int t = 0; t < b; ++t) {
+            const int p = piv[t];
+            const int x = sperm[t];
+            sperm[t] = sperm[p];
+            sperm[p] = x;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < m; i += blockDim.x) perm[f * sPerm + i] = sperm[i];
+}
+
+// ----------------------------------------------------------------- block solves
+constexpr int kSolveThreads = 1024;
+constexpr int kRmax = 4;
+
+// v (shared, column c at v + c*vs) <- L^-1 v for the unit lower n x n block of `Lm` (row-major, ld).
+template <typename T2>
+__device__ void lower_unit_solve(const T2* Lm, int ld, int n, T2* v, int vs, int nrhs) {
+    using R = typename Real<T2>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int bs = 0; bs < n; bs += 32) {
+        const int be = min(bs + 32, n);
+        if (bs > 0) {
+            for (int i = bs + warp; i < be; i += nw) {
+                T2 acc[kRmax];
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
+                for (int jj = lane; jj < bs; jj += 32) {
+                    const T2 l = Lm[int64_t(i) * ld + jj];
+#pragma unroll
+                    for (int c = 0; c < kRmax; ++c)
+                        if (c < nrhs) cfma(acc[c], l, v[c * vs + jj]);
+                }
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c) {
+                    if (c >= nrhs) break;
+                    for (int off = 16; off > 0; off >>= 1) {
+                        acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
+                        acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
+                    }
+                    if (lane == 0) v[c * vs + i] = csub(v[c * vs + i], acc[c]);
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int i = bs + lane;
+            for (int c = 0; c < nrhs; ++c) {
+                T2 x = i < be ? v[c * vs + i] : mk<T2>(R(0), R(0));
+                for (int ii = bs; ii < be; ++ii) {
+                    T2 xi;
+                    xi.x = __shfl_sync(0xffffffffu, x.x, ii - bs);
+                    xi.y = __shfl_sync(0xffffffffu, x.y, ii - bs);
+                    if (i > ii && i < be) cfms(x, Lm[int64_t(i) * ld + ii], xi);
+                }
+                if (i < be) v[c * vs + i] = x;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// v <- U^-1 v for the upper n x n block (diagonal included) of `Um`.
+template <typename T2>
+__device__ void upper_solve(const T2* Um, int ld, int n, T2* v, int vs, int nrhs) {
+    using R = typename Real<T2>::R;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int nblk = (n + 31) / 32;
+    for (int blk = nblk - 1; blk >= 0; --blk) {
+        const int bs = blk * 32, be = min(bs + 32, n);
+        if (be < n) {
+            for (int i = bs + warp; i < be; i += nw) {
+                T2 acc[kRmax];
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
+                for (int jj = be + lane; jj < n; jj += 32) {
+                    const T2 u = Um[int64_t(i) * ld + jj];
+#pragma unroll
+                    for (int c = 0; c < kRmax; ++c)
+                        if (c < nrhs) cfma(acc[c], u, v[c * vs + jj]);
+                }
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c) {
+                    if (c >= nrhs) break;
+                    for (int off = 16; off > 0; off >>= 1) {
+                        acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
+                        acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
+                    }
+                    if (lane == 0) v[c * vs + i] = csub(v[c * vs + i], acc[c]);
+                }
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            const int i = bs + lane;
+            for (int c = 0; c < nrhs; ++c) {
+                T2 x = i < be ? v[c * vs + i] : mk<T2>(R(0), R(0));
+                for (int ii = be - 1; ii >= bs; --ii) {
+                    if (i == ii) x = cmul(x, cinv(Um[int64_t(i) * ld + i]));
+                    T2 xi;
+                    xi.x = __shfl_sync(0xffffffffu, x.x, ii - bs);
+                    xi.y = __shfl_sync(0xffffffffu, x.y, ii - bs);
+                    if (i < ii && i >= bs) cfms(x, Um[int64_t(i) * ld + ii], xi);
+                }
+                if (i < be) v[c * vs + i] = x;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Forward step for slab k: permute the stacked rows, unit-lower solve, eliminate into slab k+1.
+template <typename T2>
+__global__ void __launch_bounds__(kSolveThreads) solve_fwd_kernel(const T2* U, const T2* L, int64_t sU, int64_t sL,
+                                                                  const int32_t* perm, int64_t sPerm, T2* y,
+                                                                  int64_t sY, int64_t n, int b, int k, int nz,
+                                                                  int nrhs) {
+    using R = typename Real<T2>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* t = reinterpret_cast<T2*>(smem_raw);
+    const int f = blockIdx.x;
+    const int m = (k + 1 < nz) ? 2 * b : b;
+    const int ld = 3 * b;
+    const T2* Uk = U + f * sU;
+    const T2* Lk = L + f * sL;
+    const int32_t* pk = perm + f * sPerm;
+    T2* yf = y + f * sY;
+    const int64_t base = int64_t(k) * b;
+    for (int idx = threadIdx.x; idx < m * nrhs; idx += blockDim.x) {
+        const int c = idx / m, i = idx - c * m;
+        t[c * m + i] = yf[c * n + base + pk[i]];
+    }
+    __syncthreads();
+    lower_unit_solve(Uk, ld, b, t, m, nrhs);
+    if (m == 2 * b) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = warp; i < b; i += nw) {
+            T2 acc[kRmax];
+#pragma unroll
+            for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
+            for (int jj = lane; jj < b; jj += 32) {
+                const T2 l = Lk[int64_t(i) * b + jj];
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c)
+                    if (c < nrhs) cfma(acc[c], l, t[c * m + jj]);
+            }
+#pragma unroll
+            for (int c = 0; c < kRmax; ++c) {
+                if (c >= nrhs) break;
+                for (int off = 16; off > 0; off >>= 1) {
+                    acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
+                    acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
+                }
+                if (lane == 0) t[c * m + b + i] = csub(t[c * m + b + i], acc[c]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < m * nrhs; idx += blockDim.x) {
+        const int c = idx / m, i = idx - c * m;
+        yf[c * n + base + i] = t[c * m + i];
+    }
+}
+
+// Backward step for slab k: x_k = U_kk^-1 (y_k - U_k,k+1 x_{k+1} - U_k,k+2 x_{k+2}).
+template <typename T2>
+__global__ void __launch_bounds__(kSolveThreads) solve_bwd_kernel(const T2* U, int64_t sU, T2* y, int64_t sY,
+                                                                  int64_t n, int b, int k, int nz, int nrhs) {
+    using R = typename Real<T2>::R;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* v = reinterpret_cast<T2*>(smem_raw);
+    const int f = blockIdx.x;
+    const int ld = 3 * b;
+    const T2* Uk = U + f * sU;
+    T2* yf = y + f * sY;
+    const int64_t base = int64_t(k) * b;
+    for (int idx = threadIdx.x; idx < b * nrhs; idx += blockDim.x) {
+        const int c = idx / b, i = idx - c * b;
+        v[c * b + i] = yf[c * n + base + i];
+    }
+    __syncthreads();
+    const int nfar = min(2, nz - 1 - k);  // coupled later slabs
+    if (nfar > 0) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        for (int i = warp; i < b; i += nw) {
+            T2 acc[kRmax];
+#pragma unroll
+            for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
+            for (int jj = lane; jj < nfar * b; jj += 32) {
+                const T2 u = Uk[int64_t(i) * ld + b + jj];
+#pragma unroll
+                for (int c = 0; c < kRmax; ++c)
+                    if (c < nrhs) cfma(acc[c], u, yf[c * n + base + b + jj]);
+            }
+#pragma unroll
+            for (int c = 0; c < kRmax; ++c) {
+                if (c >= nrhs) break;
+                for (int off = 16; off > 0; off >>= 1) {
+                    acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
+                    acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
+                }
+                if (lane == 0) v[c * b + i] = csub(v[c * b + i], acc[c]);
+            }
+        }
+    }
+    __syncthreads();
+    upper_solve(Uk, ld, b, v, b, nrhs);
+    for (int idx = threadIdx.x; idx < b * nrhs; idx += blockDim.x) {
+        const int c = idx / b, i = idx - c * b;
+        yf[c * n + base + i] = v[c * b + i];
+    }
+}
+
+// In-place U x = B for the upper triangle of the first n columns of each matrix;
+// B is columns [c0, c0+nrhs).
+template <typename T2>
+__global__ void __launch_bounds__(kSolveThreads) backsub_kernel(T2* G, int64_t sG, int ld, int n, int c0,
+                                                                int nrhs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T2* v = reinterpret_cast<T2*>(smem_raw);
+    T2* A = G + blockIdx.x * sG;
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+        const int c = idx / n, i = idx - c * n;
+        v[c * n + i] = A[int64_t(i) * ld + c0 + c];
+    }
+    __syncthreads();
+    upper_solve(A, ld, n, v, n, nrhs);
+    for (int idx = threadIdx.x; idx < n * nrhs; idx += blockDim.x) {
+        const int c = idx / n, i = idx - c * n;
+        A[int64_t(i) * ld + c0 + c] = v[c * n + i];
+    }
+}
+
+inline unsigned ceil_div(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+template <typename R>
+void launch_form_rows(const DevModel& m, typename Cplx<R>::T* G, int64_t sG, int ld, int F, const double* d_omega,
+                      int row_slab, int g_row0, int col_slab0, int wcols, cudaStream_t st) {
+    dim3 grid(ceil_div(m.b, 8), F);
+    ProfScope ps(PK_FORM, 0.0, st);
+    form_rows_kernel<<<grid, 256, 0, st>>>(m, G, sG, ld, d_omega, row_slab, g_row0, col_slab0, wcols);
+}
+
+template <typename R>
+int panel_width(int m) {
+    const size_t el = sizeof(typename Cplx<R>::T);
+    for (int w = 32; w >= 2; w >>= 1)
+        if (size_t(m) * w * el + 64 * (sizeof(double) + sizeof(int)) <= kMaxPanelSmem) return w;
+    return 1;
+}
+
+template <typename R>
+static int outer_nb() {
+    return sizeof(R) == 4 ? 64 : 32;
+}
+
+template <typename R>
+void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int j0, int nbw, int32_t* ipiv,
+                  int64_t sP, int32_t* status, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    const size_t smem = 64 * (sizeof(double) + sizeof(int)) + size_t(m - j0) * nbw * sizeof(T2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(panel_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem + 2048));
+        attr_set = true;
+    }
+    ProfScope ps(PK_PANEL, 0.0, st);
+    panel_kernel<T2><<<F, kPanelThreads, smem, st>>>(G, sG, ld, m, j0, nbw, ipiv, sP, status);
+}
+
+template <typename R>
+void launch_laswp(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int j, int cnt, const int32_t* ipiv,
+                  int64_t sP, int a0, int a1, int b0, int b1, cudaStream_t st) {
+    const int ncols = (a1 > a0 ? a1 - a0 : 0) + (b1 > b0 ? b1 - b0 : 0);
+    if (ncols <= 0) return;
+    dim3 grid(ceil_div(ncols, 256), F);
+    ProfScope ps(PK_LASWP, 0.0, st);
+    laswp_kernel<<<grid, 256, 0, st>>>(G, sG, ld, j, cnt, ipiv, sP, a0, a1, b0, b1);
+}
+
+template <typename R>
+void launch_trsm(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int j, int cnt, int c0, int c1,
+                 cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    if (c1 <= c0 || cnt <= 1) return;
+    const size_t smem = size_t(cnt) * cnt * sizeof(T2) + size_t(cnt) * kTrsmThreads * sizeof(T2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(trsm_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    dim3 grid(ceil_div(c1 - c0, kTrsmThreads), F);
+    ProfScope ps(PK_TRSM, 8.0 * F * double(cnt) * cnt / 2.0 * (c1 - c0), st);
+    trsm_kernel<T2><<<grid, kTrsmThreads, smem, st>>>(G, sG, ld, j, cnt, c0, c1);
+}
+
+template <typename R>
+void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0,
+                        int K, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    if (r1 <= r0 || c1 <= c0 || K <= 0) return;
+    dim3 grid(ceil_div(c1 - c0, kBN), ceil_div(r1 - r0, kBM), F);
+    ProfScope ps(PK_GEMM, 8.0 * F * double(r1 - r0) * double(c1 - c0) * K, st);
+    gemm_update_kernel<T2><<<grid, kGemmThreads, 0, st>>>(G, sG, ld, r0, r1, c0, c1, k0, K);
+}
+
+template <typename R>
+void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv, int32_t* ipiv,
+                int64_t sP, int32_t* status, cudaStream_t st) {
+    const int NB = outer_nb<R>();
+    const int nbw = std::min(panel_width<R>(m), NB);
+    for (int J = 0; J < npiv; J += NB) {
+        const int nb = std::min(NB, npiv - J);
+        for (int j = J; j < J + nb; j += nbw) {
+            const int w = std::min(nbw, J + nb - j);
+            launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, st);
+            launch_laswp<R>(G, sG, ld, F, j, w, ipiv, sP, J, j, j + w, J + nb, st);
+            if (j + w < J + nb) {
+                launch_trsm<R>(G, sG, ld, F, j, w, j + w, J + nb, st);
+                launch_gemm_update<R>(G, sG, ld, F, j + w, m, j + w, J + nb, j, w, st);
+            }
+        }
+        launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);
+        if (J + nb < ncols) {
+            launch_trsm<R>(G, sG, ld, F, J, nb, J + nb, ncols, st);
+            launch_gemm_update<R>(G, sG, ld, F, J + nb, m, J + nb, ncols, J, nb, st);
+        }
+    }
+}
+
+template <typename R>
+void launch_slab_shift(typename Cplx<R>::T* G, int64_t sG, int F, int b, int m, typename Cplx<R>::T* U, int64_t sU,
+                       typename Cplx<R>::T* L, int64_t sL, const int32_t* ipiv, int64_t sP, int32_t* perm,
+                       int64_t sPerm, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    dim3 grid(ceil_div(int64_t(b) * 3 * b, 256), F);
+    ProfScope ps(PK_SHIFT, 0.0, st);
+    slab_shift_kernel<T2><<<grid, 256, 0, st>>>(G, sG, b, m, U, sU, L, sL);
+    ProfScope ps2(PK_SHIFT, 0.0, st);
+    perm_kernel<<<F, 256, size_t(m) * sizeof(int32_t), st>>>(ipiv, sP, perm, sPerm, b, m);
+}
+
+template <typename R>
+void launch_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
+                      const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b, int k,
+                      int nz, int nrhs, int F, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(solve_fwd_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr_set = true;
+    }
+    const int m = (k + 1 < nz) ? 2 * b : b;
+    for (int c0 = 0; c0 < nrhs; c0 += kRmax) {
+        const int nc = std::min(kRmax, nrhs - c0);
+        const size_t smem = size_t(m) * nc * sizeof(T2);
+        ProfScope ps(PK_SOLVE, 8.0 * F * nc * (double(b) * b / 2.0 + (m == 2 * b ? double(b) * b : 0.0)), st);
+        solve_fwd_kernel<T2><<<F, kSolveThreads, smem, st>>>(U, L, sU, sL, perm, sPerm, y + c0 * n, sY, n, b, k, nz,
+                                                              nc);
+    }
+}
+
+template <typename R>
+void launch_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b,
+                      int k, int nz, int nrhs, int F, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(solve_bwd_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr_set = true;
+    }
+    for (int c0 = 0; c0 < nrhs; c0 += kRmax) {
+        const int nc = std::min(kRmax, nrhs - c0);
+        const size_t smem = size_t(b) * nc * sizeof(T2);
+        ProfScope ps(PK_SOLVE, 8.0 * F * nc * (double(b) * b / 2.0 + double(std::min(2, nz - 1 - k)) * b * b), st);
+        solve_bwd_kernel<T2><<<F, kSolveThreads, smem, st>>>(U, sU, y + c0 * n, sY, n, b, k, nz, nc);
+    }
+}
+
+template <typename R>
+void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, int c0, int nrhs, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(backsub_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
+        attr_set = true;
+    }
+    for (int cc = 0; cc < nrhs; cc += kRmax) {
+        const int nc = std::min(kRmax, nrhs - cc);
+        ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(n) * n / 2.0, st);
+        backsub_kernel<T2><<<F, kSolveThreads, size_t(n) * nc * sizeof(T2), st>>>(G, sG, ld, n, c0 + cc, nc);
+    }
+}
+
+#define FSI_INSTANTIATE(R)                                                                                           \
+    template void launch_form_rows<R>(const DevModel&, Cplx<R>::T*, int64_t, int, int, const double*, int, int, int, \
+                                      int, cudaStream_t);                                                            \
+    template int panel_width<R>(int);                                                                                \
+    template void launch_panel<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*,       \
+                                  cudaStream_t);                                                                     \
+    template void launch_laswp<R>(Cplx<R>::T*, int64_t, int, int, int, int, const int32_t*, int64_t, int, int, int, \
+                                  int, cudaStream_t);                                                                \
+    template void launch_trsm<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, cudaStream_t);                 \
+    template void launch_gemm_update<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, int, int, cudaStream_t); \
+    template void partial_lu<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*,         \
+                                cudaStream_t);                                                                       \
+    template void launch_slab_shift<R>(Cplx<R>::T*, int64_t, int, int, int, Cplx<R>::T*, int64_t, Cplx<R>::T*,      \
+                                       int64_t, const int32_t*, int64_t, int32_t*, int64_t, cudaStream_t);           \
+    template void launch_solve_fwd<R>(const Cplx<R>::T*, const Cplx<R>::T*, int64_t, int64_t, const int32_t*,       \
+                                      int64_t, Cplx<R>::T*, int64_t, int64_t, int, int, int, int, int, cudaStream_t); \
+    template void launch_solve_bwd<R>(const Cplx<R>::T*, int64_t, Cplx<R>::T*, int64_t, int64_t, int, int, int, int, \
+                                      int, cudaStream_t);                                                            \
+    template void launch_backsub<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, cudaStream_t);
+
+FSI_INSTANTIATE(float)
+FSI_INSTANTIATE(double)
+
+}  // namespace fsi
