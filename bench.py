@@ -4,8 +4,9 @@ Workload (the model the headline metric is quoted on): 1.5 x 1.5 x 6 m cavity
 at 24 x 24 x 96 nodes plus the shell ring, 81,792 DoF (b = 852 per slab, 96
 slabs), floor impedance, 4 seeded shell loads, 32 receivers, 481 frequencies
 20..500 Hz.  A step is one batch of `--batch` frequencies through the whole
-path: form A(w) -> block-banded LU in FP32 -> FP64 residual refinement to a
-relative residual of 1e-8 -> receivers and SPL.  value = frequencies / s over
+path: form A(w) -> block-banded LU in FP32 -> FP64 GMRES refinement
+preconditioned by the FP32 factor, to a relative residual of 1e-8 ->
+receivers and SPL.  value = frequencies / s over
 all ranks.  The factor store of one batch (~70 GB) is far larger than L2, so no
 separate L2 flush is needed between steps.
 
@@ -190,9 +191,9 @@ def main():
     ws_bytes = api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers))
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
+    kw = dict(precision=args.precision, batch=B, max_refine=60, tol=1e-8, workspace=ws, allow_noconv=True)
     for s in range(args.warmup):
-        api.frf_sweep_full(model, batch_freqs(s), F, rcv, precision=args.precision, batch=B, max_refine=20,
-                           tol=1e-8, workspace=ws)
+        api.frf_sweep_full(model, batch_freqs(s), F, rcv, **kw)
     torch.cuda.synchronize()
     if pg:
         pg.barrier()
@@ -203,12 +204,13 @@ def main():
     kern_flops = np.zeros(8)
     kern_n = np.zeros(8, dtype=np.int64)
     launches = 0
+    unconv = 0
     iters = []
     torch.cuda.synchronize()
     ev0.record(stream)
     for s in range(args.warmup, nsteps):
-        r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, precision=args.precision, batch=B, max_refine=20,
-                               tol=1e-8, workspace=ws, profile=True)
+        r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, profile=True, **kw)
+        unconv += int(r.stats.n_unconverged)
         kern_ms += np.array(r.stats.kernel_ms[:])
         kern_flops += np.array(r.stats.kernel_flops[:])
         kern_n += np.array(r.stats.kernel_launches[:])
@@ -236,8 +238,7 @@ def main():
         t0 = time.perf_counter()
         ne = max(1, min(2, args.steps))
         for s in range(ne):
-            api.frf_sweep_full(model, batch_freqs(nsteps + s), Fview, rh, precision=args.precision, batch=B,
-                               max_refine=20, tol=1e-8, host_io=True, workspace=ws)
+            api.frf_sweep_full(model, batch_freqs(nsteps + s), Fview, rh, host_io=True, **kw)
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
         h2d = Fh.size * 16 + rh.size * 4
@@ -254,8 +255,8 @@ def main():
         r64 = api.frf_sweep_full(model, fs, F, rcv, precision="fp64", batch=len(fs), max_refine=1)
         torch.cuda.synchronize()
         t64 = time.perf_counter() - t0
-        rmix = api.frf_sweep_full(model, fs, F, rcv, precision=args.precision, batch=len(fs), max_refine=20,
-                                  tol=1e-8)
+        rmix = api.frf_sweep_full(model, fs, F, rcv, precision=args.precision, batch=len(fs), max_refine=60,
+                                  tol=1e-8, allow_noconv=True)
         p64 = r64.p.cpu().numpy()
         pm = rmix.p.cpu().numpy()
         fp64 = {"value": len(fs) / t64, "unit": UNIT, "sample": f"{len(fs)} frequencies",
@@ -293,7 +294,8 @@ def main():
                            "l2": "inputs larger than L2 (factor store ~70 GB per batch)"},
                 "roofline": roofline, "kernels": shares, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "fp64_full_order": fp64,
-                "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters))},
+                "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters)), "unconverged": unconv,
+                                 "method": "GMRES(20) on the FP64 system, FP32 band-LU preconditioner"},
                 "peaks_source": src}
         print(json.dumps(line), flush=True)
     if pg:

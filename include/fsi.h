@@ -107,7 +107,17 @@ typedef struct {
                                   /*    the copies happen inside the call           */
     int profile;                  /* 1: time every kernel launch with CUDA events   */
                                   /*    on `stream` and report per-kernel totals    */
+    int refine;                   /* FSI_REFINE_IR or FSI_REFINE_GMRES              */
+    int restart;                  /* GMRES restart length (0: 20)                   */
 } fsi_solve_opts;
+
+/* Refinement of the low-precision factor's solution against the FP64 residual:
+ * plain refinement x <- x + LU^-1 r (converges when cond(A) u_low < 1), or
+ * flexible GMRES on the FP64 system right-preconditioned by the factor (the
+ * GMRES of paper Sec. 3.2 used as refinement), which also converges at the low
+ * frequencies where the thin shell drives cond(A) to 1e7-1e8.  max_refine
+ * caps the number of preconditioned solves in both cases. */
+enum { FSI_REFINE_IR = 0, FSI_REFINE_GMRES = 1 };
 
 /* Kernel classes of the per-kernel totals in fsi_sweep_stats. */
 enum {

@@ -38,7 +38,7 @@ class fsi_dims(C.Structure):
 
 class fsi_solve_opts(C.Structure):
     _fields_ = [("precision", c_int), ("batch", c_int), ("max_refine", c_int), ("tol", C.c_double),
-                ("host_io", c_int), ("profile", c_int)]
+                ("host_io", c_int), ("profile", c_int), ("refine", c_int), ("restart", c_int)]
 
 
 class fsi_sweep_stats(C.Structure):

@@ -96,9 +96,15 @@ def fsi_assemble(spec, device="cuda") -> DeviceModel:
     return DeviceModel(spec=spec, dims=dims, buf=view)
 
 
-def _opts(precision, batch, max_refine, tol, host_io, profile=False) -> L.fsi_solve_opts:
+REFINE = {"ir": 0, "gmres": 1}
+
+
+def _opts(precision, batch, max_refine, tol, host_io, profile=False, refine="gmres",
+          restart=20) -> L.fsi_solve_opts:
     o = L.fsi_solve_opts()
     o.profile = int(bool(profile))
+    o.refine = REFINE[refine] if isinstance(refine, str) else int(refine)
+    o.restart = int(restart)
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.batch = int(batch)
     o.max_refine = int(max_refine)
@@ -108,9 +114,9 @@ def _opts(precision, batch, max_refine, tol, host_io, profile=False) -> L.fsi_so
 
 
 def frf_sweep_workspace(model: DeviceModel, precision="fp32_ir", batch=8, nrhs=1, nrcv=1,
-                        host_io=False) -> int:
+                        host_io=False, refine="gmres", restart=20) -> int:
     lib = L.load()
-    o = _opts(precision, batch, 1, 1e-8, host_io)
+    o = _opts(precision, batch, 1, 1e-8, host_io, refine=refine, restart=restart)
     nb = C.c_size_t()
     L.check(lib.frf_sweep_workspace(C.byref(model.dims), C.byref(o), nrhs, nrcv, C.byref(nb)),
             "frf_sweep_workspace")
@@ -128,7 +134,7 @@ class SweepResult:
 
 def frf_sweep_full(model: DeviceModel, freqs_hz: Sequence[float], F, rcv, precision="fp32_ir",
                    batch=8, max_refine=10, tol=1e-8, host_io=False, workspace=None,
-                   allow_noconv=False, profile=False, outputs=None) -> SweepResult:
+                   allow_noconv=False, profile=False, refine=None, restart=20) -> SweepResult:
     """Full-order sweep.  F: n x nrhs complex128 (torch CUDA tensor, or numpy with host_io);
     rcv: receiver DoF indices (torch int32 CUDA tensor, or numpy with host_io)."""
     torch = _torch()
@@ -156,7 +162,9 @@ def frf_sweep_full(model: DeviceModel, freqs_hz: Sequence[float], F, rcv, precis
         p = torch.empty((nf, nrcv, nrhs), dtype=torch.complex128, device=F.device)
         spl = torch.empty((nf, nrcv, nrhs), dtype=torch.float64, device=F.device)
         pp, sp = _ptr(p), _ptr(spl)
-    o = _opts(precision, min(batch, nf), max_refine, tol, host_io, profile)
+    if refine is None:
+        refine = "ir" if precision == "fp64" else "gmres"
+    o = _opts(precision, min(batch, nf), max_refine, tol, host_io, profile, refine, restart)
     need = C.c_size_t()
     L.check(lib.frf_sweep_workspace(C.byref(model.dims), C.byref(o), nrhs, nrcv, C.byref(need)),
             "frf_sweep_workspace")

@@ -120,9 +120,11 @@ struct SweepWS {
     int32_t* rcvd = nullptr;
     double2* pb = nullptr;
     double* splb = nullptr;
+    void* gws = nullptr;
+    size_t gws_bytes = 0;
     int64_t sV = 0;
 
-    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io) {
+    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int gmres_restart) {
         fc.carve(c, d, F);
         sV = int64_t(nrhs) * d.n;
         omega = c.take<double>(F);
@@ -137,8 +139,17 @@ struct SweepWS {
             pb = c.take<double2>(size_t(F) * nrcv * nrhs);
             splb = c.take<double>(size_t(F) * nrcv * nrhs);
         }
+        if (gmres_restart > 0) {
+            gws_bytes = gmres_ws_bytes(d.n, F * nrhs, gmres_restart);
+            gws = c.take<char>(gws_bytes);
+        }
     }
 };
+
+int gmres_restart_of(const fsi_solve_opts& o) {
+    if (o.refine != FSI_REFINE_GMRES) return 0;
+    return o.restart > 0 ? o.restart : 20;
+}
 
 fsi_status check_dims(const fsi_dims* d) {
     FSI_REQUIRE(d, "dims is NULL");
@@ -147,10 +158,10 @@ fsi_status check_dims(const fsi_dims* d) {
 }
 
 template <typename R>
-size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io) {
+size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int restart) {
     Carver c(nullptr, 0);
     SweepWS<R> w;
-    w.carve(c, d, F, nrhs, nrcv, host_io);
+    w.carve(c, d, F, nrhs, nrcv, host_io, restart);
     return align_up(c.used);
 }
 
@@ -203,7 +214,8 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     const bool host_io = o.host_io != 0;
     Carver c(ws, ws_bytes);
     SweepWS<R> w;
-    w.carve(c, d, Fb_max, nrhs, nrcv, host_io);
+    const int restart = gmres_restart_of(o);
+    w.carve(c, d, Fb_max, nrhs, nrcv, host_io, restart);
     if (!c.fits()) {
         set_error("workspace too small: need " + std::to_string(align_up(c.used)) + " bytes");
         return FSI_ENOMEM;
@@ -232,8 +244,12 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         FSI_CUDA(cudaMemcpyAsync(w.omega, om.data(), sizeof(double) * Fb, cudaMemcpyHostToDevice, st));
         fsi_status s = factor_batch<R>(m, w.fc, Fb, w.omega, st);
         if (s != FSI_OK) return s;
-        s = ir_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.sV, max_it, tol,
-                        it_done, rel, st);
+        if (restart > 0)
+            s = fgmres_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.sV,
+                                restart, (max_it + restart - 1) / restart, tol, w.gws, w.gws_bytes, it_done, rel, st);
+        else
+            s = ir_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.sV, max_it,
+                            tol, it_done, rel, st);
         if (s != FSI_OK) return s;
         FSI_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
         double2* pdst = host_io ? w.pb : reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs;
@@ -279,6 +295,8 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     return FSI_OK;
 }
 
+template fsi_status solve_batch<float>(const DevModel&, Factor<float>&, int, float2*, int64_t, int, cudaStream_t);
+template fsi_status solve_batch<double>(const DevModel&, Factor<double>&, int, double2*, int64_t, int, cudaStream_t);
 template fsi_status factor_batch<float>(const DevModel&, Factor<float>&, int, const double*, cudaStream_t);
 template fsi_status factor_batch<double>(const DevModel&, Factor<double>&, int, const double*, cudaStream_t);
 template fsi_status ir_solve<float>(const DevModel&, Factor<float>&, int, const double*, const double2*, int,
@@ -363,8 +381,9 @@ fsi_status frf_sweep_workspace(const fsi_dims* dims, const fsi_solve_opts* opts,
     if (s != FSI_OK) return s;
     FSI_REQUIRE(opts && bytes && nrhs > 0 && nrcv > 0 && opts->batch > 0, "bad sweep workspace arguments");
     const bool hio = opts->host_io != 0;
-    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio)
-                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio);
+    const int rs = gmres_restart_of(*opts);
+    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio, rs)
+                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio, rs);
     return FSI_OK;
 }
 

@@ -52,4 +52,18 @@ fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_om
                     double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms, int64_t sV,
                     int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
 
+template <typename R>
+fsi_status solve_batch(const DevModel& m, Factor<R>& fc, int F, typename Cplx<R>::T* y, int64_t sY, int nrhs,
+                       cudaStream_t st);
+
+// Flexible GMRES on the FP64 scaled system, right preconditioned by the factor in
+// precision R, restarted every `restart` iterations, at most max_cycles cycles;
+// same outputs as ir_solve (it_done counts preconditioned solves).
+size_t gmres_ws_bytes(int64_t n, int P, int restart);
+template <typename R>
+fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev,
+                        int nrhs, double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
+                        int64_t sV, int restart, int max_cycles, double tol, void* gws, size_t gws_bytes,
+                        std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
+
 }  // namespace fsi
