@@ -194,6 +194,28 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
                           int64_t sA, int32_t* ipiv, void* ws, size_t ws_bytes,
                           int* n_singular_out, void* stream);
 
+/* Allocation-free variant of fsi_batched_lu (the paper has no counterpart; it
+ * is a service to callers).  Some callers cannot allocate device memory: code
+ * inside a memory pool that forbids new allocations, real-time loops that must
+ * not wait on an allocator, or hosts whose interface has no way to pass a
+ * workspace.  This entry point takes no workspace and calls no allocator
+ * (no cudaMalloc, cudaFree or allocating library routine).  The kernels'
+ * scratch (one pivot-status flag per matrix and a counter) lives in a fixed
+ * 16 KiB device array inside the library, which every GPU that loads the
+ * library holds until the process exits.
+ *   - batch is limited to 4095 matrices; larger batches return FSI_EINVAL
+ *     with a message (split the call, or use fsi_batched_lu).
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the one array and each call clears the part it uses
+ *     before use: calls that overlap on the GPU (different streams, or
+ *     different host threads on one device) race and must be serialised.
+ * Arguments, results and errors are those of fsi_batched_lu; it synchronizes
+ * the stream when n_singular_out is not NULL. */
+fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, int ncols, int npiv, void* A,
+                                  int64_t ld, int64_t sA, int32_t* ipiv, int* n_singular_out,
+                                  void* stream);
+
 typedef struct {
     int precision;                /* factorisation per expansion point             */
     int max_refine;               /* refinement cap per moment solve (FP32_IR)     */

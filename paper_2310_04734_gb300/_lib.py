@@ -69,6 +69,8 @@ SIGNATURES = {
     "fsi_lu_workspace": (c_int, [c_int, c_int, C.POINTER(c_size_t)]),
     "fsi_batched_lu": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, C.c_int64, C.c_int64,
                                c_void_p, c_void_p, c_size_t, C.POINTER(c_int), c_void_p]),
+    "fsi_batched_lu_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, C.c_int64, C.c_int64,
+                                       c_void_p, C.POINTER(c_int), c_void_p]),
     "rom_workspace": (c_int, [C.POINTER(fsi_dims), c_int, c_int, c_int, C.POINTER(fsi_rom_opts),
                               C.POINTER(c_size_t)]),
     "rom_build": (c_int, [C.POINTER(fsi_dims), c_void_p, c_double_p, c_int, c_int, c_void_p, c_int,

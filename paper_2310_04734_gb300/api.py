@@ -214,6 +214,26 @@ def fsi_batched_lu(A, npiv: int):
     return ipiv, nsing.value
 
 
+def fsi_batched_lu_noalloc(A, npiv: int):
+    """Same as fsi_batched_lu, through the entry point that allocates nothing.
+
+    For callers that cannot allocate device memory: no workspace is created
+    here or in the library; the kernels' status flags live in a fixed device
+    array inside libfsi.so (at most 4095 matrices per call).  Calls that overlap
+    on the GPU share that array and must not run concurrently.
+    """
+    lib = L.load()
+    assert A.is_contiguous() and A.dim() == 3
+    torch = _torch()
+    batch, m, ncols = A.shape
+    prec = FSI_FP64 if A.dtype == torch.complex128 else FSI_FP32_IR
+    ipiv = torch.empty((batch, npiv), dtype=torch.int32, device=A.device)
+    nsing = C.c_int(0)
+    L.check(lib.fsi_batched_lu_noalloc(prec, batch, m, ncols, npiv, _ptr(A), ncols, m * ncols, _ptr(ipiv),
+                                       C.byref(nsing), _stream_ptr()), "fsi_batched_lu_noalloc")
+    return ipiv, nsing.value
+
+
 def _rom_opts(precision="fp32_ir", max_refine=10, tol=1e-10, second_order=-1):
     o = L.fsi_rom_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
