@@ -52,7 +52,9 @@ typedef enum {
 
 typedef enum {
     FSI_FP64 = 0,         /* factor and solve in FP64 (the plain full-order sweep)  */
-    FSI_FP32_IR = 1       /* factor in FP32, FP64 residual iterative refinement     */
+    FSI_FP32_IR = 1,      /* factor in FP32, FP64 residual iterative refinement     */
+    FSI_TF32X3_IR = 2     /* as FSI_FP32_IR, trailing updates on the tensor cores   */
+                          /* (tcgen05, TF32 hi/lo split, 3 products, FP32 sums)      */
 } fsi_precision;
 
 /* Geometry and materials of the coupled model (paper Sec. 2; loss factor
@@ -186,7 +188,8 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
  * columns, rows npiv..m-1 hold the multipliers (cols < npiv) and the Schur
  * complement (cols >= npiv); ipiv[i*npiv + j] is the row swapped with row j
  * (LAPACK getrf convention, 0-based).  precision selects FP64 or FP32 data:
- * A points to fsi_c64 (FP64) or to {float re, im} pairs (FP32).  ws: device
+ * A points to fsi_c64 (FP64) or to {float re, im} pairs (FSI_FP32_IR, and
+ * FSI_TF32X3_IR with the tensor-core trailing updates).  ws: device
  * workspace of fsi_lu_workspace bytes.  status_out (host, nullable) gets the
  * number of matrices that met a zero or non-finite pivot. */
 fsi_status fsi_lu_workspace(int batch, int m, size_t* bytes);

@@ -16,7 +16,8 @@ from . import _lib as L
 
 FSI_FP64 = 0
 FSI_FP32_IR = 1
-PRECISIONS = {"fp64": FSI_FP64, "fp32_ir": FSI_FP32_IR}
+FSI_TF32X3_IR = 2
+PRECISIONS = {"fp64": FSI_FP64, "fp32_ir": FSI_FP32_IR, "tf32x3_ir": FSI_TF32X3_IR}
 
 
 def _torch():
@@ -197,13 +198,14 @@ def fsi_residual(model: DeviceModel, freqs_hz, X, F):
     return R.transpose(1, 2)
 
 
-def fsi_batched_lu(A, npiv: int):
-    """In-place batched partial LU of row-major A [batch][m][ncols] (complex64 or complex128 CUDA)."""
+def fsi_batched_lu(A, npiv: int, tensor_cores: bool = False):
+    """In-place batched partial LU of row-major A [batch][m][ncols] (complex64 or complex128 CUDA);
+    complex64 with tensor_cores=True runs the trailing updates on tcgen05 (3xTF32)."""
     torch = _torch()
     lib = L.load()
     assert A.is_contiguous() and A.dim() == 3
     batch, m, ncols = A.shape
-    prec = FSI_FP64 if A.dtype == torch.complex128 else FSI_FP32_IR
+    prec = FSI_FP64 if A.dtype == torch.complex128 else (FSI_TF32X3_IR if tensor_cores else FSI_FP32_IR)
     ipiv = torch.empty((batch, npiv), dtype=torch.int32, device=A.device)
     need = C.c_size_t()
     L.check(lib.fsi_lu_workspace(batch, m, C.byref(need)), "fsi_lu_workspace")

@@ -75,13 +75,15 @@ template <typename R>
 fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d_omega, cudaStream_t st) {
     const int b = m.b, nz = m.nz, ld = 3 * b;
     FSI_CUDA(cudaMemsetAsync(fc.status, 0, sizeof(int32_t) * F, st));
+    FSI_CUDA(cudaMemsetAsync(fc.tc_err, 0, sizeof(int32_t), st));
     launch_form_rows<R>(m, fc.G, fc.sG, ld, F, d_omega, 0, 0, 0, ld, st);
     FSI_CHECK_LAUNCH();
     for (int k = 0; k < nz; ++k) {
         const int m_rows = (k + 1 < nz) ? 2 * b : b;
         const int ncols = std::min(3, nz - k) * b;
         if (k + 1 < nz) launch_form_rows<R>(m, fc.G, fc.sG, ld, F, d_omega, k + 1, b, k, ld, st);
-        partial_lu<R>(fc.G, fc.sG, ld, F, m_rows, ncols, b, fc.ipiv + int64_t(k) * b, fc.sP, fc.status, st);
+        partial_lu<R>(fc.G, fc.sG, ld, F, m_rows, ncols, b, fc.ipiv + int64_t(k) * b, fc.sP, fc.status, st,
+                      fc.use_tc ? fc.tc_err : nullptr);
         launch_slab_shift<R>(fc.G, fc.sG, F, b, m_rows, fc.U + int64_t(k) * b * 3 * b, fc.sU,
                              fc.L + int64_t(k) * b * b, fc.sL, fc.ipiv + int64_t(k) * b, fc.sP,
                              fc.perm + int64_t(k) * 2 * b, fc.sPerm, st);
@@ -95,11 +97,11 @@ fsi_status solve_batch(const DevModel& m, Factor<R>& fc, int F, typename Cplx<R>
                        cudaStream_t st) {
     const int b = m.b, nz = m.nz;
     for (int k = 0; k < nz; ++k) {
-        launch_solve_fwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.L + int64_t(k) * b * b, fc.sU, fc.sL,
-                            fc.perm + int64_t(k) * 2 * b, fc.sPerm, y, sY, m.n, b, k, nz, nrhs, F, st);
+        launch_slab_solve_fwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.L + int64_t(k) * b * b, fc.sU, fc.sL,
+                                 fc.perm + int64_t(k) * 2 * b, fc.sPerm, y, sY, m.n, b, k, nz, nrhs, F, fc.tmp, st);
     }
     for (int k = nz - 1; k >= 0; --k) {
-        launch_solve_bwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.sU, y, sY, m.n, b, k, nz, nrhs, F, st);
+        launch_slab_solve_bwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.sU, y, sY, m.n, b, k, nz, nrhs, F, fc.tmp, st);
     }
     FSI_CHECK_LAUNCH();
     return FSI_OK;
@@ -125,7 +127,7 @@ struct SweepWS {
     int64_t sV = 0;
 
     void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int gmres_restart) {
-        fc.carve(c, d, F);
+        fc.carve(c, d, F, nrhs);
         sV = int64_t(nrhs) * d.n;
         omega = c.take<double>(F);
         xhat = c.take<double2>(size_t(F) * sV);
@@ -221,6 +223,7 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         return FSI_ENOMEM;
     }
     const DevModel m = dev_model(d, d_model);
+    w.fc.use_tc = (o.precision == FSI_TF32X3_IR);
     prof().reset(o.profile != 0);
     const double2* Fdev = reinterpret_cast<const double2*>(F);
     const int32_t* rcvdev = rcv;
@@ -252,6 +255,8 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
                             tol, it_done, rel, st);
         if (s != FSI_OK) return s;
         FSI_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
+        int32_t htc = 0;
+        FSI_CUDA(cudaMemcpyAsync(&htc, w.fc.tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         double2* pdst = host_io ? w.pb : reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs;
         double* sdst = host_io ? w.splb : (spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr);
         launch_receivers(m, w.omega, Fb, w.xhat, w.sV, rcvdev, nrcv, nrhs, pdst, sdst, st);
@@ -265,6 +270,10 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         }
         FSI_CUDA(cudaStreamSynchronize(st));
         prof().collect();
+        if (htc) {
+            set_error("a tensor-core update gave up waiting for its MMAs");
+            return FSI_ETIMEOUT;
+        }
         for (int f = 0; f < Fb; ++f) {
             const int its = it_done[f] < 0 ? max_it : it_done[f];
             if (iters_out) iters_out[f0 + f] = its;
@@ -395,7 +404,8 @@ fsi_status frf_sweep_full(const fsi_dims* dims, const void* d_model, const doubl
     if (s != FSI_OK) return s;
     FSI_REQUIRE(d_model && f_hz && F && rcv && opts && ws && p_out, "NULL argument");
     FSI_REQUIRE(nf > 0 && nrhs > 0 && nrcv > 0 && opts->batch > 0, "nf, nrhs, nrcv, batch must be positive");
-    FSI_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR, "unknown precision");
+    FSI_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR || opts->precision == FSI_TF32X3_IR,
+                "unknown precision");
     for (int i = 0; i < nf; ++i) FSI_REQUIRE(f_hz[i] > 0.0 && std::isfinite(f_hz[i]), "frequencies must be > 0");
     if (opts->host_io)
         for (int i = 0; i < nrcv; ++i) FSI_REQUIRE(rcv[i] >= 0 && rcv[i] < dims->n, "receiver index out of range");
@@ -426,7 +436,7 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
 
 fsi_status fsi_lu_workspace(int batch, int m, size_t* bytes) {
     FSI_REQUIRE(batch > 0 && m > 0 && bytes, "bad lu workspace arguments");
-    *bytes = align_up(sizeof(int32_t) * size_t(batch));
+    *bytes = align_up(sizeof(int32_t) * size_t(batch + 1));
     return FSI_OK;
 }
 
@@ -434,23 +444,28 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
                           int32_t* ipiv, void* ws, size_t ws_bytes, int* n_singular_out, void* stream) {
     FSI_REQUIRE(A && ipiv && ws && batch > 0 && m > 0 && ncols > 0, "bad batched lu arguments");
     FSI_REQUIRE(npiv > 0 && npiv <= m && npiv <= ncols && ld >= ncols && sA >= ld * m, "bad batched lu shape");
-    FSI_REQUIRE(ws_bytes >= sizeof(int32_t) * size_t(batch), "workspace too small");
+    FSI_REQUIRE(ws_bytes >= sizeof(int32_t) * size_t(batch + 1), "workspace too small");
     FSI_REQUIRE(m <= 8192, "m too large for the panel kernel");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int32_t* status = static_cast<int32_t*>(ws);
-    FSI_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * batch, st));
+    FSI_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * (batch + 1), st));
     if (precision == FSI_FP64)
         partial_lu<double>(static_cast<double2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st);
     else
-        partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st);
+        partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st,
+                          precision == FSI_TF32X3_IR ? status + batch : nullptr);
     FSI_CHECK_LAUNCH();
-    if (n_singular_out) {
-        std::vector<int32_t> h(batch);
-        FSI_CUDA(cudaMemcpyAsync(h.data(), status, sizeof(int32_t) * batch, cudaMemcpyDeviceToHost, st));
+    if (n_singular_out || precision == FSI_TF32X3_IR) {
+        std::vector<int32_t> h(batch + 1);
+        FSI_CUDA(cudaMemcpyAsync(h.data(), status, sizeof(int32_t) * (batch + 1), cudaMemcpyDeviceToHost, st));
         FSI_CUDA(cudaStreamSynchronize(st));
         int cnt = 0;
-        for (int v : h) cnt += v != 0;
-        *n_singular_out = cnt;
+        for (int i = 0; i < batch; ++i) cnt += h[i] != 0;
+        if (n_singular_out) *n_singular_out = cnt;
+        if (precision == FSI_TF32X3_IR && h[batch]) {
+            set_error("a tensor-core update gave up waiting for its MMAs");
+            return FSI_ETIMEOUT;
+        }
     }
     return FSI_OK;
 }

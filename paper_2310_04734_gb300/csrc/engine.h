@@ -21,9 +21,12 @@ struct Factor {
     int32_t* ipiv = nullptr;
     int32_t* perm = nullptr;
     int32_t* status = nullptr;
+    T2* tmp = nullptr;   // [F][nrhs][2b] staging of the slab solves
+    int32_t* tc_err = nullptr;   // set: trailing updates on the tensor cores (FP32 storage only)
+    bool use_tc = false;
     int64_t sG = 0, sU = 0, sL = 0, sP = 0, sPerm = 0;
 
-    void carve(Carver& c, const fsi_dims& d, int F) {
+    void carve(Carver& c, const fsi_dims& d, int F, int nrhs) {
         const int64_t b = d.b, nz = d.nz;
         sG = 2 * b * 3 * b;
         sU = nz * b * 3 * b;
@@ -36,6 +39,8 @@ struct Factor {
         ipiv = c.take<int32_t>(size_t(F) * sP);
         perm = c.take<int32_t>(size_t(F) * sPerm);
         status = c.take<int32_t>(size_t(F));
+        tmp = c.take<T2>(size_t(F) * nrhs * 2 * b);
+        tc_err = c.take<int32_t>(1);
     }
 };
 

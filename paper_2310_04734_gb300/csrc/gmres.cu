@@ -210,7 +210,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
     GM_CUDA(cudaMemsetAsync(xhat, 0, sizeof(double2) * P * n, st));
     GM_CUDA(cudaMemcpyAsync(hn.data(), fnorms, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
     GM_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> pdone(P, -1);
+    std::vector<int> pdone(P, -1), inner_done(P, -1);
     int total_it = 0;
     std::vector<double> prel(P, 1.0);
     for (int p = 0; p < P; ++p) prel[p] = hf[p] > 0 ? std::sqrt(hn[p] / hf[p]) : 0.0;
@@ -219,7 +219,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
         int nact = 0;
         for (int p = 0; p < P; ++p) {
             hact[p] = prel[p] > tol ? 1 : 0;
-            if (!hact[p] && pdone[p] < 0) pdone[p] = total_it;
+            if (!hact[p] && pdone[p] < 0) pdone[p] = inner_done[p] >= 0 ? inner_done[p] : total_it;
             nact += hact[p];
         }
         if (nact == 0) break;
@@ -305,8 +305,12 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
                 g[p][j] = cc * g[p][j];
                 kdim[p] = j + 1;
                 const double est = std::abs(g[p][j + 1]) / std::sqrt(hf[p]);
-                if (est <= tol * 0.5 || hj1 == 0.0) live[p] = 0;
-                else any = true;
+                if (est <= tol * 0.5 || hj1 == 0.0) {
+                    live[p] = 0;
+                    if (inner_done[p] < 0) inner_done[p] = total_it;
+                } else {
+                    any = true;
+                }
             }
             if (!any || j + 1 == mm) {
                 ++j;
@@ -339,8 +343,13 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
                         true, st);
         GM_CUDA(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
         GM_CUDA(cudaStreamSynchronize(st));
-        for (int p = 0; p < P; ++p) prel[p] = hf[p] > 0 ? std::sqrt(hn[p] / hf[p]) : 0.0;
+        for (int p = 0; p < P; ++p) {
+            prel[p] = hf[p] > 0 ? std::sqrt(hn[p] / hf[p]) : 0.0;
+            if (prel[p] > tol) inner_done[p] = -1;   // the estimate was optimistic: keep iterating
+        }
     }
+    for (int p = 0; p < P; ++p)
+        if (pdone[p] < 0 && prel[p] <= tol) pdone[p] = inner_done[p] >= 0 ? inner_done[p] : total_it;
     it_done.assign(Fb, -1);
     rel.assign(Fb, 0.0);
     for (int f = 0; f < Fb; ++f) {
@@ -351,7 +360,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
             const int p = f * nrhs + cc;
             r = std::max(r, prel[p]);
             if (prel[p] > tol) ok = false;
-            it = std::max(it, pdone[p] < 0 ? total_it : std::max(pdone[p], 1));
+            it = std::max(it, pdone[p] < 0 ? total_it : std::max(pdone[p], 1));   // solves until this pair converged
         }
         rel[f] = r;
         it_done[f] = ok ? it : -1;

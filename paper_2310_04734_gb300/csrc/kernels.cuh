@@ -119,12 +119,18 @@ template <typename R>
 void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1,
                         int k0, int K, cudaStream_t st);
 
-// Batched partial LU driver on device matrices (uses the kernels above).
+// Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (3xTF32); err gets 1 if a
+// bounded wait gave up.
+void launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
+                      int32_t* err, cudaStream_t st);
+
+// Batched partial LU driver on device matrices (uses the kernels above).  With tc_err != NULL
+// (FP32 only) the outer trailing updates run on the tensor cores.
 template <typename R>
 int panel_width(int m);
 template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv,
-                int32_t* ipiv, int64_t sP, int32_t* status, cudaStream_t st);
+                int32_t* ipiv, int64_t sP, int32_t* status, cudaStream_t st, int32_t* tc_err = nullptr);
 
 // After a slab step: save factor rows and multipliers, turn ipiv into a row
 // permutation of the stacked rows, and move the Schur tail to the top rows.
@@ -133,15 +139,15 @@ void launch_slab_shift(typename Cplx<R>::T* G, int64_t sG, int F, int b, int m, 
                        int64_t sU, typename Cplx<R>::T* L, int64_t sL, const int32_t* ipiv, int64_t sP,
                        int32_t* perm, int64_t sPerm, cudaStream_t st);
 
-// Forward / backward block-banded solve of one slab for nrhs right-hand sides
-// (y is [F][nrhs][n], U/L/perm point at slab k of the store).
+// Slab solves: per slab a triangle launch (one CTA per frequency) and a batched
+// matrix-vector launch for the off-diagonal factor blocks; tmp is unused.
 template <typename R>
-void launch_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
-                      const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n,
-                      int b, int k, int nz, int nrhs, int F, cudaStream_t st);
+void launch_slab_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
+                           const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b,
+                           int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st);
 template <typename R>
-void launch_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY,
-                      int64_t n, int b, int k, int nz, int nrhs, int F, cudaStream_t st);
+void launch_slab_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY, int64_t n,
+                           int b, int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st);
 
 // U x = B in place for the upper triangle of the first n columns; B = columns [c0, c0+nrhs).
 template <typename R>

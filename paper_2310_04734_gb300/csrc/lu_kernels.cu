@@ -313,53 +313,6 @@ __global__ void perm_kernel(const int32_t* ipiv, int64_t sP, int32_t* perm, int6
 constexpr int kSolveThreads = 1024;
 constexpr int kRmax = 4;
 
-// v (shared, column c at v + c*vs) <- L^-1 v for the unit lower n x n block of `Lm` (row-major, ld).
-template <typename T2>
-__device__ void lower_unit_solve(const T2* Lm, int ld, int n, T2* v, int vs, int nrhs) {
-    using R = typename Real<T2>::R;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int bs = 0; bs < n; bs += 32) {
-        const int be = min(bs + 32, n);
-        if (bs > 0) {
-            for (int i = bs + warp; i < be; i += nw) {
-                T2 acc[kRmax];
-#pragma unroll
-                for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
-                for (int jj = lane; jj < bs; jj += 32) {
-                    const T2 l = Lm[int64_t(i) * ld + jj];
-#pragma unroll
-                    for (int c = 0; c < kRmax; ++c)
-                        if (c < nrhs) cfma(acc[c], l, v[c * vs + jj]);
-                }
-#pragma unroll
-                for (int c = 0; c < kRmax; ++c) {
-                    if (c >= nrhs) break;
-                    for (int off = 16; off > 0; off >>= 1) {
-                        acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
-                        acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
-                    }
-                    if (lane == 0) v[c * vs + i] = csub(v[c * vs + i], acc[c]);
-                }
-            }
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const int i = bs + lane;
-            for (int c = 0; c < nrhs; ++c) {
-                T2 x = i < be ? v[c * vs + i] : mk<T2>(R(0), R(0));
-                for (int ii = bs; ii < be; ++ii) {
-                    T2 xi;
-                    xi.x = __shfl_sync(0xffffffffu, x.x, ii - bs);
-                    xi.y = __shfl_sync(0xffffffffu, x.y, ii - bs);
-                    if (i > ii && i < be) cfms(x, Lm[int64_t(i) * ld + ii], xi);
-                }
-                if (i < be) v[c * vs + i] = x;
-            }
-        }
-        __syncthreads();
-    }
-}
-
 // v <- U^-1 v for the upper n x n block (diagonal included) of `Um`.
 template <typename T2>
 __device__ void upper_solve(const T2* Um, int ld, int n, T2* v, int vs, int nrhs) {
@@ -406,108 +359,6 @@ __device__ void upper_solve(const T2* Um, int ld, int n, T2* v, int vs, int nrhs
             }
         }
         __syncthreads();
-    }
-}
-
-// Forward step for slab k: permute the stacked rows, unit-lower solve, eliminate into slab k+1.
-template <typename T2>
-__global__ void __launch_bounds__(kSolveThreads) solve_fwd_kernel(const T2* U, const T2* L, int64_t sU, int64_t sL,
-                                                                  const int32_t* perm, int64_t sPerm, T2* y,
-                                                                  int64_t sY, int64_t n, int b, int k, int nz,
-                                                                  int nrhs) {
-    using R = typename Real<T2>::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* t = reinterpret_cast<T2*>(smem_raw);
-    const int f = blockIdx.x;
-    const int m = (k + 1 < nz) ? 2 * b : b;
-    const int ld = 3 * b;
-    const T2* Uk = U + f * sU;
-    const T2* Lk = L + f * sL;
-    const int32_t* pk = perm + f * sPerm;
-    T2* yf = y + f * sY;
-    const int64_t base = int64_t(k) * b;
-    for (int idx = threadIdx.x; idx < m * nrhs; idx += blockDim.x) {
-        const int c = idx / m, i = idx - c * m;
-        t[c * m + i] = yf[c * n + base + pk[i]];
-    }
-    __syncthreads();
-    lower_unit_solve(Uk, ld, b, t, m, nrhs);
-    if (m == 2 * b) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int i = warp; i < b; i += nw) {
-            T2 acc[kRmax];
-#pragma unroll
-            for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
-            for (int jj = lane; jj < b; jj += 32) {
-                const T2 l = Lk[int64_t(i) * b + jj];
-#pragma unroll
-                for (int c = 0; c < kRmax; ++c)
-                    if (c < nrhs) cfma(acc[c], l, t[c * m + jj]);
-            }
-#pragma unroll
-            for (int c = 0; c < kRmax; ++c) {
-                if (c >= nrhs) break;
-                for (int off = 16; off > 0; off >>= 1) {
-                    acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
-                    acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
-                }
-                if (lane == 0) t[c * m + b + i] = csub(t[c * m + b + i], acc[c]);
-            }
-        }
-        __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < m * nrhs; idx += blockDim.x) {
-        const int c = idx / m, i = idx - c * m;
-        yf[c * n + base + i] = t[c * m + i];
-    }
-}
-
-// Backward step for slab k: x_k = U_kk^-1 (y_k - U_k,k+1 x_{k+1} - U_k,k+2 x_{k+2}).
-template <typename T2>
-__global__ void __launch_bounds__(kSolveThreads) solve_bwd_kernel(const T2* U, int64_t sU, T2* y, int64_t sY,
-                                                                  int64_t n, int b, int k, int nz, int nrhs) {
-    using R = typename Real<T2>::R;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T2* v = reinterpret_cast<T2*>(smem_raw);
-    const int f = blockIdx.x;
-    const int ld = 3 * b;
-    const T2* Uk = U + f * sU;
-    T2* yf = y + f * sY;
-    const int64_t base = int64_t(k) * b;
-    for (int idx = threadIdx.x; idx < b * nrhs; idx += blockDim.x) {
-        const int c = idx / b, i = idx - c * b;
-        v[c * b + i] = yf[c * n + base + i];
-    }
-    __syncthreads();
-    const int nfar = min(2, nz - 1 - k);  // coupled later slabs
-    if (nfar > 0) {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        for (int i = warp; i < b; i += nw) {
-            T2 acc[kRmax];
-#pragma unroll
-            for (int c = 0; c < kRmax; ++c) acc[c] = mk<T2>(R(0), R(0));
-            for (int jj = lane; jj < nfar * b; jj += 32) {
-                const T2 u = Uk[int64_t(i) * ld + b + jj];
-#pragma unroll
-                for (int c = 0; c < kRmax; ++c)
-                    if (c < nrhs) cfma(acc[c], u, yf[c * n + base + b + jj]);
-            }
-#pragma unroll
-            for (int c = 0; c < kRmax; ++c) {
-                if (c >= nrhs) break;
-                for (int off = 16; off > 0; off >>= 1) {
-                    acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
-                    acc[c].y += __shfl_down_sync(0xffffffffu, acc[c].y, off);
-                }
-                if (lane == 0) v[c * b + i] = csub(v[c * b + i], acc[c]);
-            }
-        }
-    }
-    __syncthreads();
-    upper_solve(Uk, ld, b, v, b, nrhs);
-    for (int idx = threadIdx.x; idx < b * nrhs; idx += blockDim.x) {
-        const int c = idx / b, i = idx - c * b;
-        yf[c * n + base + i] = v[c * b + i];
     }
 }
 
@@ -608,8 +459,20 @@ void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r
 }
 
 template <typename R>
+void trailing_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
+                     int32_t* tc_err, cudaStream_t st) {
+    if constexpr (sizeof(R) == 4) {
+        if (tc_err) {
+            launch_tc_update(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc_err, st);
+            return;
+        }
+    }
+    launch_gemm_update<R>(G, sG, ld, F, r0, r1, c0, c1, k0, K, st);
+}
+
+template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv, int32_t* ipiv,
-                int64_t sP, int32_t* status, cudaStream_t st) {
+                int64_t sP, int32_t* status, cudaStream_t st, int32_t* tc_err) {
     const int NB = outer_nb<R>();
     const int nbw = std::min(panel_width<R>(m), NB);
     for (int J = 0; J < npiv; J += NB) {
@@ -626,7 +489,7 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
         launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);
         if (J + nb < ncols) {
             launch_trsm<R>(G, sG, ld, F, J, nb, J + nb, ncols, st);
-            launch_gemm_update<R>(G, sG, ld, F, J + nb, m, J + nb, ncols, J, nb, st);
+            trailing_update<R>(G, sG, ld, F, J + nb, m, J + nb, ncols, J, nb, tc_err, st);
         }
     }
 }
@@ -641,43 +504,6 @@ void launch_slab_shift(typename Cplx<R>::T* G, int64_t sG, int F, int b, int m, 
     slab_shift_kernel<T2><<<grid, 256, 0, st>>>(G, sG, b, m, U, sU, L, sL);
     ProfScope ps2(PK_SHIFT, 0.0, st);
     perm_kernel<<<F, 256, size_t(m) * sizeof(int32_t), st>>>(ipiv, sP, perm, sPerm, b, m);
-}
-
-template <typename R>
-void launch_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
-                      const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b, int k,
-                      int nz, int nrhs, int F, cudaStream_t st) {
-    using T2 = typename Cplx<R>::T;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(solve_fwd_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
-    const int m = (k + 1 < nz) ? 2 * b : b;
-    for (int c0 = 0; c0 < nrhs; c0 += kRmax) {
-        const int nc = std::min(kRmax, nrhs - c0);
-        const size_t smem = size_t(m) * nc * sizeof(T2);
-        ProfScope ps(PK_SOLVE, 8.0 * F * nc * (double(b) * b / 2.0 + (m == 2 * b ? double(b) * b : 0.0)), st);
-        solve_fwd_kernel<T2><<<F, kSolveThreads, smem, st>>>(U, L, sU, sL, perm, sPerm, y + c0 * n, sY, n, b, k, nz,
-                                                              nc);
-    }
-}
-
-template <typename R>
-void launch_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b,
-                      int k, int nz, int nrhs, int F, cudaStream_t st) {
-    using T2 = typename Cplx<R>::T;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(solve_bwd_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
-        attr_set = true;
-    }
-    for (int c0 = 0; c0 < nrhs; c0 += kRmax) {
-        const int nc = std::min(kRmax, nrhs - c0);
-        const size_t smem = size_t(b) * nc * sizeof(T2);
-        ProfScope ps(PK_SOLVE, 8.0 * F * nc * (double(b) * b / 2.0 + double(std::min(2, nz - 1 - k)) * b * b), st);
-        solve_bwd_kernel<T2><<<F, kSolveThreads, smem, st>>>(U, sU, y + c0 * n, sY, n, b, k, nz, nc);
-    }
 }
 
 template <typename R>
@@ -706,13 +532,9 @@ void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, in
     template void launch_trsm<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, cudaStream_t);                 \
     template void launch_gemm_update<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, int, int, cudaStream_t); \
     template void partial_lu<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*,         \
-                                cudaStream_t);                                                                       \
+                                cudaStream_t, int32_t*);                                                             \
     template void launch_slab_shift<R>(Cplx<R>::T*, int64_t, int, int, int, Cplx<R>::T*, int64_t, Cplx<R>::T*,      \
                                        int64_t, const int32_t*, int64_t, int32_t*, int64_t, cudaStream_t);           \
-    template void launch_solve_fwd<R>(const Cplx<R>::T*, const Cplx<R>::T*, int64_t, int64_t, const int32_t*,       \
-                                      int64_t, Cplx<R>::T*, int64_t, int64_t, int, int, int, int, int, cudaStream_t); \
-    template void launch_solve_bwd<R>(const Cplx<R>::T*, int64_t, Cplx<R>::T*, int64_t, int64_t, int, int, int, int, \
-                                      int, cudaStream_t);                                                            \
     template void launch_backsub<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, cudaStream_t);
 
 FSI_INSTANTIATE(float)

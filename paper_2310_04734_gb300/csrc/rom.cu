@@ -380,7 +380,7 @@ struct RomWS {
     int64_t sV;
 
     void carve(Carver& c, const fsi_dims& d, int nrhs, int q, int kmax) {
-        fc.carve(c, d, 1);
+        fc.carve(c, d, 1, nrhs);
         sV = int64_t(nrhs) * d.n;
         omega = c.take<double>(1);
         xhat = c.take<double2>(sV);
