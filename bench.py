@@ -245,6 +245,7 @@ def main():
     unconv = 0
     iters = []
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for s in range(args.warmup, nsteps):
         r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, profile=True, **kw)
@@ -256,6 +257,7 @@ def main():
         iters.extend(r.iters.tolist())
     ev1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
     t_ms = ev0.elapsed_time(ev1)
     if pg:

@@ -118,6 +118,7 @@ struct SweepWS {
     T2* y = nullptr;
     double* norms = nullptr;
     double* fnorms = nullptr;
+    double* absn = nullptr;
     double2* Fd = nullptr;
     int32_t* rcvd = nullptr;
     double2* pb = nullptr;
@@ -135,6 +136,7 @@ struct SweepWS {
         y = c.take<T2>(size_t(F) * sV);
         norms = c.take<double>(size_t(F) * nrhs);
         fnorms = c.take<double>(size_t(F) * nrhs);
+        absn = c.take<double>(size_t(F) * nrhs);
         if (host_io) {
             Fd = c.take<double2>(size_t(d.n) * nrhs);
             rcvd = c.take<int32_t>(nrcv);
@@ -169,9 +171,10 @@ size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io
 
 template <typename R>
 fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev, int nrhs,
-                    double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms, int64_t sV,
-                    int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st) {
-    std::vector<double> hn(size_t(Fb) * nrhs), hf(size_t(Fb) * nrhs);
+                    double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
+                    double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done,
+                    std::vector<double>& rel, cudaStream_t st) {
+    std::vector<double> hn(size_t(Fb) * nrhs), hf(size_t(Fb) * nrhs), ha(size_t(Fb) * nrhs);
     FSI_CUDA(cudaMemsetAsync(fnorms, 0, sizeof(double) * Fb * nrhs, st));
     launch_residual(m, d_omega, 0.0, Fb, nullptr, sV, Bdev, nrhs, rhat, sV, fnorms, true, st);
     FSI_CHECK_LAUNCH();
@@ -186,20 +189,26 @@ fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_om
         if (s != FSI_OK) return s;
         launch_update<R>(xhat, sV, norms, y, sV, m.n, nrhs, Fb, nullptr, st);
         FSI_CUDA(cudaMemsetAsync(norms, 0, sizeof(double) * Fb * nrhs, st));
-        launch_residual(m, d_omega, 0.0, Fb, xhat, sV, Bdev, nrhs, rhat, sV, norms, true, st);
+        FSI_CUDA(cudaMemsetAsync(absn, 0, sizeof(double) * Fb * nrhs, st));
+        launch_residual(m, d_omega, 0.0, Fb, xhat, sV, Bdev, nrhs, rhat, sV, norms, true, st, absn);
         FSI_CHECK_LAUNCH();
         FSI_CUDA(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
+        FSI_CUDA(cudaMemcpyAsync(ha.data(), absn, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
         FSI_CUDA(cudaStreamSynchronize(st));
         bool all = true;
         for (int f = 0; f < Fb; ++f) {
             double r = 0.0;
+            bool conv = true;
             for (int cc = 0; cc < nrhs; ++cc) {
-                const double den = hf[size_t(f) * nrhs + cc];
-                const double v = den > 0 ? std::sqrt(hn[size_t(f) * nrhs + cc] / den) : 0.0;
+                const size_t q = size_t(f) * nrhs + cc;
+                const double den = hf[q];
+                const double v = den > 0 ? std::sqrt(hn[q] / den) : 0.0;
                 r = std::max(r, std::isfinite(v) ? v : INFINITY);
+                const bool at_floor = std::sqrt(hn[q]) <= kResFloor * std::sqrt(ha[q]);
+                if (!(v <= tol || at_floor)) conv = false;
             }
             rel[f] = r;
-            if (it_done[f] < 0 && r <= tol) it_done[f] = it;
+            if (it_done[f] < 0 && conv) it_done[f] = it;
             if (it_done[f] < 0) all = false;
         }
         if (all) break;
@@ -248,10 +257,10 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         fsi_status s = factor_batch<R>(m, w.fc, Fb, w.omega, st);
         if (s != FSI_OK) return s;
         if (restart > 0)
-            s = fgmres_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.sV,
+            s = fgmres_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.absn, w.sV,
                                 restart, (max_it + restart - 1) / restart, tol, w.gws, w.gws_bytes, it_done, rel, st);
         else
-            s = ir_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.sV, max_it,
+            s = ir_solve<R>(m, w.fc, Fb, w.omega, Fdev, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.absn, w.sV, max_it,
                             tol, it_done, rel, st);
         if (s != FSI_OK) return s;
         FSI_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
@@ -309,10 +318,10 @@ template fsi_status solve_batch<double>(const DevModel&, Factor<double>&, int, d
 template fsi_status factor_batch<float>(const DevModel&, Factor<float>&, int, const double*, cudaStream_t);
 template fsi_status factor_batch<double>(const DevModel&, Factor<double>&, int, const double*, cudaStream_t);
 template fsi_status ir_solve<float>(const DevModel&, Factor<float>&, int, const double*, const double2*, int,
-                                    double2*, double2*, float2*, double*, double*, int64_t, int, double,
+                                    double2*, double2*, float2*, double*, double*, double*, int64_t, int, double,
                                     std::vector<int>&, std::vector<double>&, cudaStream_t);
 template fsi_status ir_solve<double>(const DevModel&, Factor<double>&, int, const double*, const double2*, int,
-                                     double2*, double2*, double2*, double*, double*, int64_t, int, double,
+                                     double2*, double2*, double2*, double*, double*, double*, int64_t, int, double,
                                      std::vector<int>&, std::vector<double>&, cudaStream_t);
 
 }  // namespace fsi

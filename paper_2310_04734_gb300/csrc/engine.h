@@ -45,17 +45,24 @@ struct Factor {
 };
 
 
+// A scaled residual below kResFloor * u64 * |rs o (|A| |cs o x| + |F|)| is at the
+// rounding level of its own FP64 evaluation (and of a backward-stable FP64 solve):
+// refinement cannot reduce it further, so a pair there counts as converged even
+// if its relative residual is above the requested tolerance.
+constexpr double kResFloor = 8.0 * 1.1102230246251565e-16;
+
 template <typename R>
 fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d_omega, cudaStream_t st);
 
 // Iterative refinement of A(w_f) x = B for every batch member: FP64 scaled
 // residual, correction by the stored factors in precision R.  On return xhat
 // holds the scaled solution (x = cs o xhat); it_done[f] is the first iteration
-// whose relative residual reached tol (-1: not reached), rel[f] the last one.
+// whose relative residual reached tol or the rounding floor (-1: neither), rel[f]
+// the last relative residual.  absn: F*nrhs scratch for the floor.
 template <typename R>
 fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev, int nrhs,
-                    double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms, int64_t sV,
-                    int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
+                    double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
+                    double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
 
 template <typename R>
 fsi_status solve_batch(const DevModel& m, Factor<R>& fc, int F, typename Cplx<R>::T* y, int64_t sY, int nrhs,
@@ -68,7 +75,7 @@ size_t gmres_ws_bytes(int64_t n, int P, int restart);
 template <typename R>
 fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev,
                         int nrhs, double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
-                        int64_t sV, int restart, int max_cycles, double tol, void* gws, size_t gws_bytes,
+                        double* absn, int64_t sV, int restart, int max_cycles, double tol, void* gws, size_t gws_bytes,
                         std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
 
 }  // namespace fsi

@@ -179,7 +179,7 @@ size_t gmres_ws_bytes(int64_t n, int P, int m) {
 template <typename R>
 fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev,
                         int nrhs, double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
-                        int64_t sV, int restart, int max_cycles, double tol, void* gws, size_t gws_bytes,
+                        double* absn, int64_t sV, int restart, int max_cycles, double tol, void* gws, size_t gws_bytes,
                         std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
     const int64_t n = m.n;
@@ -200,7 +200,8 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
     }
     const int64_t sVb = int64_t(P) * n;   // stride between basis vectors
     (void)sV;
-    std::vector<double> hf(P), hn(P), hs(P);
+    std::vector<double> hf(P), hn(P), hs(P), ha(P);
+    std::vector<double> flo(P, 0.0);   // relative rounding floor of the last explicit residual
     std::vector<int32_t> hact(P);
     // r = R f, |R f|
     GM_CUDA(cudaMemsetAsync(fnorms, 0, sizeof(double) * P, st));
@@ -214,11 +215,12 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
     int total_it = 0;
     std::vector<double> prel(P, 1.0);
     for (int p = 0; p < P; ++p) prel[p] = hf[p] > 0 ? std::sqrt(hn[p] / hf[p]) : 0.0;
+    auto conv = [&](int p) { return prel[p] <= std::max(tol, flo[p]); };
     for (int cyc = 0; cyc < max_cycles; ++cyc) {
         // active pairs: not yet at tol
         int nact = 0;
         for (int p = 0; p < P; ++p) {
-            hact[p] = prel[p] > tol ? 1 : 0;
+            hact[p] = conv(p) ? 0 : 1;
             if (!hact[p] && pdone[p] < 0) pdone[p] = inner_done[p] >= 0 ? inner_done[p] : total_it;
             nact += hact[p];
         }
@@ -305,7 +307,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
                 g[p][j] = cc * g[p][j];
                 kdim[p] = j + 1;
                 const double est = std::abs(g[p][j + 1]) / std::sqrt(hf[p]);
-                if (est <= tol * 0.5 || hj1 == 0.0) {
+                if (est <= 0.5 * std::max(tol, flo[p]) || hj1 == 0.0) {
                     live[p] = 0;
                     if (inner_done[p] < 0) inner_done[p] = total_it;
                 } else {
@@ -339,17 +341,20 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
         bcombine_kernel<<<dim3(cdiv(n, 256), P), 256, 0, st>>>(Z, sVb, n, nj, yd, xhat);
         // explicit residual
         GM_CUDA(cudaMemsetAsync(norms, 0, sizeof(double) * P, st));
+        GM_CUDA(cudaMemsetAsync(absn, 0, sizeof(double) * P, st));
         launch_residual(m, d_omega, 0.0, Fb, xhat, int64_t(nrhs) * n, Bdev, nrhs, rhat, int64_t(nrhs) * n, norms,
-                        true, st);
+                        true, st, absn);
         GM_CUDA(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
+        GM_CUDA(cudaMemcpyAsync(ha.data(), absn, sizeof(double) * P, cudaMemcpyDeviceToHost, st));
         GM_CUDA(cudaStreamSynchronize(st));
         for (int p = 0; p < P; ++p) {
             prel[p] = hf[p] > 0 ? std::sqrt(hn[p] / hf[p]) : 0.0;
-            if (prel[p] > tol) inner_done[p] = -1;   // the estimate was optimistic: keep iterating
+            flo[p] = hf[p] > 0 ? kResFloor * std::sqrt(ha[p] / hf[p]) : 0.0;
+            if (!conv(p)) inner_done[p] = -1;   // the estimate was optimistic: keep iterating
         }
     }
     for (int p = 0; p < P; ++p)
-        if (pdone[p] < 0 && prel[p] <= tol) pdone[p] = inner_done[p] >= 0 ? inner_done[p] : total_it;
+        if (pdone[p] < 0 && conv(p)) pdone[p] = inner_done[p] >= 0 ? inner_done[p] : total_it;
     it_done.assign(Fb, -1);
     rel.assign(Fb, 0.0);
     for (int f = 0; f < Fb; ++f) {
@@ -359,7 +364,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
         for (int cc = 0; cc < nrhs; ++cc) {
             const int p = f * nrhs + cc;
             r = std::max(r, prel[p]);
-            if (prel[p] > tol) ok = false;
+            if (!conv(p)) ok = false;
             it = std::max(it, pdone[p] < 0 ? total_it : std::max(pdone[p], 1));   // solves until this pair converged
         }
         rel[f] = r;
@@ -370,10 +375,10 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
 }
 
 template fsi_status fgmres_solve<float>(const DevModel&, Factor<float>&, int, const double*, const double2*, int,
-                                        double2*, double2*, float2*, double*, double*, int64_t, int, int, double,
+                                        double2*, double2*, float2*, double*, double*, double*, int64_t, int, int, double,
                                         void*, size_t, std::vector<int>&, std::vector<double>&, cudaStream_t);
 template fsi_status fgmres_solve<double>(const DevModel&, Factor<double>&, int, const double*, const double2*, int,
-                                         double2*, double2*, double2*, double*, double*, int64_t, int, int, double,
+                                         double2*, double2*, double2*, double*, double*, double*, int64_t, int, int, double,
                                          void*, size_t, std::vector<int>&, std::vector<double>&, cudaStream_t);
 
 }  // namespace fsi

@@ -139,6 +139,10 @@ void launch_slab_shift(typename Cplx<R>::T* G, int64_t sG, int F, int b, int m, 
                        int64_t sU, typename Cplx<R>::T* L, int64_t sL, const int32_t* ipiv, int64_t sP,
                        int32_t* perm, int64_t sPerm, cudaStream_t st);
 
+// Complex FP32 C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] B[k0:k0+K, c0:c1] in each of F matrices (SIMT).
+void launch_cgemm_f32(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
+                      cudaStream_t st);
+
 // Slab solves: per slab a triangle launch (one CTA per frequency) and a batched
 // matrix-vector launch for the off-diagonal factor blocks; tmp is unused.
 template <typename R>
@@ -156,9 +160,11 @@ void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, in
 // FP64 residual r = rs o (F - A(w_f) (cs o x)) (scaled) or F - A x (unscaled);
 // x may be NULL (x = 0).  Accumulates |r|^2 per (f, column) into norms if non-NULL.
 // omega per batch member from d_omega, or the scalar omega0 when d_omega is NULL.
+// absn (optional) accumulates |rs o (|A| |cs o x| + |F|)|^2 per (f, column): the size of the
+// terms whose FP64 rounding bounds the attainable residual.
 void launch_residual(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x,
                      int64_t sX, const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms,
-                     bool scaled, cudaStream_t st);
+                     bool scaled, cudaStream_t st, double* absn = nullptr);
 // y = (T)(r / s) with s = sqrt(norms) per (f, column)
 template <typename R>
 void launch_to_low(const double2* r, int64_t sR, const double* norms, typename Cplx<R>::T* y, int64_t sY,

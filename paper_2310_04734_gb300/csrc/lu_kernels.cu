@@ -214,7 +214,8 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(T2* G, int64_t sG, i
 }
 
 // ----------------------------------------------------------------- gemm update
-// C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] * B[k0:k0+K, c0:c1] within one matrix of the batch.
+// C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] * B[k0:k0+K, c0:c1] within one matrix of the batch
+// (FP64; the FP32 update is the register-tiled kernel of cgemm_f32.cu).
 constexpr int kBM = 64, kBN = 64, kBK = 16, kGemmThreads = 256;
 template <typename T2>
 __global__ void __launch_bounds__(kGemmThreads) gemm_update_kernel(T2* G, int64_t sG, int ld, int r0, int r1,
@@ -453,6 +454,10 @@ void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r
                         int K, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
     if (r1 <= r0 || c1 <= c0 || K <= 0) return;
+    if constexpr (sizeof(R) == 4) {
+        launch_cgemm_f32(G, sG, ld, F, r0, r1, c0, c1, k0, K, st);
+        return;
+    }
     dim3 grid(ceil_div(c1 - c0, kBN), ceil_div(r1 - r0, kBM), F);
     ProfScope ps(PK_GEMM, 8.0 * F * double(r1 - r0) * double(c1 - c0) * K, st);
     gemm_update_kernel<T2><<<grid, kGemmThreads, 0, st>>>(G, sG, ld, r0, r1, c0, c1, k0, K);

@@ -374,7 +374,7 @@ struct RomWS {
     double* omega;
     double2 *xhat, *rhat, *X, *B, *W;
     T2* y;
-    double *norms, *fnorms;
+    double *norms, *fnorms, *absn;
     CgsBufs cg;
     double2 *Qs, *Ps;
     int64_t sV;
@@ -391,6 +391,7 @@ struct RomWS {
         y = c.take<T2>(sV);
         norms = c.take<double>(nrhs);
         fnorms = c.take<double>(nrhs);
+        absn = c.take<double>(nrhs);
         const int kk = std::max(kmax, q) + 1;
         cg.partial = c.take<double2>(size_t(kChunks) * kk * std::max(nrhs, 1));
         cg.H = c.take<double2>(size_t(kk) * std::max(nrhs, 1));
@@ -414,7 +415,7 @@ fsi_status shifted_solve(const DevModel& m, RomWS<R>& w, double om, const double
                          double tol, double sign, double2* X, cudaStream_t st) {
     std::vector<int> done;
     std::vector<double> rel;
-    fsi_status s = ir_solve<R>(m, w.fc, 1, w.omega, B, nr, w.xhat, w.rhat, w.y, w.norms, w.fnorms,
+    fsi_status s = ir_solve<R>(m, w.fc, 1, w.omega, B, nr, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.absn,
                                int64_t(nr) * m.n, max_it, tol, done, rel, st);
     if (s != FSI_OK) return s;
     unscale_kernel<<<cdiv(m.n * nr, 256), 256, 0, st>>>(m, om, w.xhat, X, nr, sign);

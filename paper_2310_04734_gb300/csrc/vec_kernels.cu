@@ -15,16 +15,16 @@ constexpr int kResRmax = 8;
 
 __global__ void residual_kernel(DevModel m, const double* omega, double omega0, const double2* x, int64_t sX,
                                 const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms, int nstride,
-                                int ncol0, bool scaled) {
+                                int ncol0, bool scaled, double* absn) {
     const int f = blockIdx.y;
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     const double w = omega ? omega[f] : omega0;
     double2 acc[kResRmax];
 #pragma unroll
     for (int c = 0; c < kResRmax; ++c) acc[c] = make_double2(0.0, 0.0);
-    double nrm[kResRmax];
+    double nrm[kResRmax], sab[kResRmax], anr[kResRmax];
 #pragma unroll
-    for (int c = 0; c < kResRmax; ++c) nrm[c] = 0.0;
+    for (int c = 0; c < kResRmax; ++c) nrm[c] = sab[c] = anr[c] = 0.0;
     if (i < m.n) {
         if (x) {
             const double2* xf = x + f * sX;
@@ -40,6 +40,15 @@ __global__ void residual_kernel(DevModel m, const double* omega, double omega0, 
 #pragma unroll
                 for (int c = 0; c < kResRmax; ++c)
                     if (c < nrhs) cfma(acc[c], a, xf[c * m.n + col]);
+                if (absn) {
+                    const double aa = hypot(a.x, a.y);
+#pragma unroll
+                    for (int c = 0; c < kResRmax; ++c)
+                        if (c < nrhs) {
+                            const double2 xv = xf[c * m.n + col];
+                            sab[c] += aa * hypot(xv.x, xv.y);
+                        }
+                }
             }
         }
         const double rs = scaled ? row_scale(m, i, w) : 1.0;
@@ -51,6 +60,18 @@ __global__ void residual_kernel(DevModel m, const double* omega, double omega0, 
             const double2 v = make_double2(rs * (fv.x - acc[c].x), rs * (fv.y - acc[c].y));
             rf[c * m.n + i] = v;
             nrm[c] = v.x * v.x + v.y * v.y;
+            const double t = rs * (sab[c] + hypot(fv.x, fv.y));
+            anr[c] = t * t;
+        }
+    }
+    if (absn) {
+        const int lane = threadIdx.x & 31;
+#pragma unroll
+        for (int c = 0; c < kResRmax; ++c) {
+            if (c >= nrhs) break;
+            double v = anr[c];
+            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+            if (lane == 0 && v != 0.0) atomicAdd(&absn[f * nstride + ncol0 + c], v);
         }
     }
     if (norms) {
@@ -116,13 +137,13 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return unsigned((a + b - 1) / b
 
 void launch_residual(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
                      const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms, bool scaled,
-                     cudaStream_t st) {
+                     cudaStream_t st, double* absn) {
     for (int c0 = 0; c0 < nrhs; c0 += kResRmax) {
         const int nc = nrhs - c0 < kResRmax ? nrhs - c0 : kResRmax;
         dim3 grid(ceil_div(m.n, 256), F);
         ProfScope ps(PK_RESID, 0.0, st);
         residual_kernel<<<grid, 256, 0, st>>>(m, d_omega, omega0, x ? x + c0 * m.n : nullptr, sX, Fm + c0 * m.n, nc,
-                                              r + c0 * m.n, sR, norms, nrhs, c0, scaled);
+                                              r + c0 * m.n, sR, norms, nrhs, c0, scaled, absn);
     }
 }
 
