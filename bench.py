@@ -238,9 +238,9 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    kern_ms = np.zeros(8)
-    kern_flops = np.zeros(8)
-    kern_n = np.zeros(8, dtype=np.int64)
+    kern_ms = np.zeros(12)
+    kern_flops = np.zeros(12)
+    kern_n = np.zeros(12, dtype=np.int64)
     launches = 0
     unconv = 0
     iters = []
@@ -327,7 +327,8 @@ def main():
                     "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
     shares = {k: {"ms": float(kern_ms[i]), "launches": int(kern_n[i]),
                   "share": float(kern_ms[i] / max(kern_ms.sum(), 1e-9))}
-              for i, k in enumerate(["gemm", "panel", "trsm", "laswp", "form", "shift", "solve", "resid"])}
+              for i, k in enumerate(["gemm", "panel", "trsm", "laswp", "form", "shift", "solve_tri", "resid",
+                                         "solve_gemv"])}
 
     if rank == 0:
         cpu = None

@@ -129,9 +129,11 @@ enum {
     FSI_K_LASWP = 3,              /* row interchanges                               */
     FSI_K_FORM = 4,               /* dense scaled rows of A(w) from the CSR values  */
     FSI_K_SHIFT = 5,              /* factor store write-out and window shift        */
-    FSI_K_SOLVE = 6,              /* forward / backward slab solves                 */
+    FSI_K_SOLVE = 6,              /* triangles of the forward / backward slab solves */
     FSI_K_RESID = 7,              /* FP64 residual, refinement updates, receivers   */
-    FSI_K_COUNT = 8
+    FSI_K_GEMV = 8,               /* off-diagonal factor blocks in the slab solves  */
+    FSI_K_COUNT = 9,
+    FSI_K_SLOTS = 12              /* array length in fsi_sweep_stats (room to grow) */
 };
 
 typedef struct {
@@ -142,9 +144,9 @@ typedef struct {
     int64_t launches;             /* kernel launches made by the call               */
     /* with opts.profile: summed event time (ms), algorithmic real flops (complex  */
     /* multiply-add = 8) and launch count per kernel class FSI_K_*                  */
-    double kernel_ms[8];
-    double kernel_flops[8];
-    int64_t kernel_launches[8];
+    double kernel_ms[FSI_K_SLOTS];
+    double kernel_flops[FSI_K_SLOTS];
+    int64_t kernel_launches[FSI_K_SLOTS];
 } fsi_sweep_stats;
 
 /* Workspace bytes needed by frf_sweep_full for these options.  Host only. */

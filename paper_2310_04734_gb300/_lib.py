@@ -43,8 +43,8 @@ class fsi_solve_opts(C.Structure):
 
 class fsi_sweep_stats(C.Structure):
     _fields_ = [("n_done", c_int), ("max_iters", c_int), ("max_relres", C.c_double),
-                ("n_unconverged", c_int), ("launches", C.c_int64), ("kernel_ms", C.c_double * 8),
-                ("kernel_flops", C.c_double * 8), ("kernel_launches", C.c_int64 * 8)]
+                ("n_unconverged", c_int), ("launches", C.c_int64), ("kernel_ms", C.c_double * 12),
+                ("kernel_flops", C.c_double * 12), ("kernel_launches", C.c_int64 * 12)]
 
 
 class fsi_rom_opts(C.Structure):

@@ -94,14 +94,16 @@ fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d
 
 template <typename R>
 fsi_status solve_batch(const DevModel& m, Factor<R>& fc, int F, typename Cplx<R>::T* y, int64_t sY, int nrhs,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int32_t* flist, int nF) {
     const int b = m.b, nz = m.nz;
+    const int Fl = flist ? nF : F;
+    if (Fl <= 0) return FSI_OK;
     for (int k = 0; k < nz; ++k) {
         launch_slab_solve_fwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.L + int64_t(k) * b * b, fc.sU, fc.sL,
-                                 fc.perm + int64_t(k) * 2 * b, fc.sPerm, y, sY, m.n, b, k, nz, nrhs, F, fc.tmp, st);
+                                 fc.perm + int64_t(k) * 2 * b, fc.sPerm, y, sY, m.n, b, k, nz, nrhs, Fl, flist, st);
     }
     for (int k = nz - 1; k >= 0; --k) {
-        launch_slab_solve_bwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.sU, y, sY, m.n, b, k, nz, nrhs, F, fc.tmp, st);
+        launch_slab_solve_bwd<R>(fc.U + int64_t(k) * b * 3 * b, fc.sU, y, sY, m.n, b, k, nz, nrhs, Fl, flist, st);
     }
     FSI_CHECK_LAUNCH();
     return FSI_OK;
@@ -295,6 +297,9 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         S.n_done = f0 + Fb;
     }
     S.launches = prof().launches;
+    static_assert(int(PK_COUNT) == int(FSI_K_COUNT) && int(FSI_K_COUNT) <= int(FSI_K_SLOTS) &&
+                      int(PK_GEMV) == int(FSI_K_GEMV) && int(PK_SOLVE) == int(FSI_K_SOLVE),
+                  "kernel classes of the profiler and the C ABI differ");
     for (int i = 0; i < PK_COUNT; ++i) {
         S.kernel_ms[i] = prof().ms[i];
         S.kernel_flops[i] = prof().flops[i];
@@ -313,8 +318,10 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     return FSI_OK;
 }
 
-template fsi_status solve_batch<float>(const DevModel&, Factor<float>&, int, float2*, int64_t, int, cudaStream_t);
-template fsi_status solve_batch<double>(const DevModel&, Factor<double>&, int, double2*, int64_t, int, cudaStream_t);
+template fsi_status solve_batch<float>(const DevModel&, Factor<float>&, int, float2*, int64_t, int, cudaStream_t,
+                                       const int32_t*, int);
+template fsi_status solve_batch<double>(const DevModel&, Factor<double>&, int, double2*, int64_t, int, cudaStream_t,
+                                        const int32_t*, int);
 template fsi_status factor_batch<float>(const DevModel&, Factor<float>&, int, const double*, cudaStream_t);
 template fsi_status factor_batch<double>(const DevModel&, Factor<double>&, int, const double*, cudaStream_t);
 template fsi_status ir_solve<float>(const DevModel&, Factor<float>&, int, const double*, const double2*, int,

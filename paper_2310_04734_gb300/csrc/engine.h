@@ -21,7 +21,6 @@ struct Factor {
     int32_t* ipiv = nullptr;
     int32_t* perm = nullptr;
     int32_t* status = nullptr;
-    T2* tmp = nullptr;   // [F][nrhs][2b] staging of the slab solves
     int32_t* tc_err = nullptr;   // set: trailing updates on the tensor cores (FP32 storage only)
     bool use_tc = false;
     int64_t sG = 0, sU = 0, sL = 0, sP = 0, sPerm = 0;
@@ -39,7 +38,6 @@ struct Factor {
         ipiv = c.take<int32_t>(size_t(F) * sP);
         perm = c.take<int32_t>(size_t(F) * sPerm);
         status = c.take<int32_t>(size_t(F));
-        tmp = c.take<T2>(size_t(F) * nrhs * 2 * b);
         tc_err = c.take<int32_t>(1);
     }
 };
@@ -64,9 +62,11 @@ fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_om
                     double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
                     double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
 
+// Forward and backward slab solves of y (F frequencies, nrhs columns each, stride sY);
+// with flist (device, nF entries) only the listed frequencies are solved.
 template <typename R>
 fsi_status solve_batch(const DevModel& m, Factor<R>& fc, int F, typename Cplx<R>::T* y, int64_t sY, int nrhs,
-                       cudaStream_t st);
+                       cudaStream_t st, const int32_t* flist = nullptr, int nF = 0);
 
 // Flexible GMRES on the FP64 scaled system, right preconditioned by the factor in
 // precision R, restarted every `restart` iterations, at most max_cycles cycles;

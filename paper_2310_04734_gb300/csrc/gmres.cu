@@ -173,6 +173,7 @@ size_t gmres_ws_bytes(int64_t n, int P, int m) {
     c.take<double>(P);                        // nrm
     c.take<double>(P);                        // scale
     c.take<int32_t>(P);                       // active
+    c.take<int32_t>(P);                       // frequencies with an active pair
     return align_up(c.used);
 }
 
@@ -194,6 +195,7 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
     double* nrm = c.take<double>(P);
     double* scl = c.take<double>(P);
     int32_t* act = c.take<int32_t>(P);
+    int32_t* flist = c.take<int32_t>(P);
     if (!c.fits()) {
         set_error("GMRES workspace too small");
         return FSI_ENOMEM;
@@ -203,6 +205,8 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
     std::vector<double> hf(P), hn(P), hs(P), ha(P);
     std::vector<double> flo(P, 0.0);   // relative rounding floor of the last explicit residual
     std::vector<int32_t> hact(P);
+    std::vector<int32_t> hfl;
+    hfl.reserve(Fb);
     // r = R f, |R f|
     GM_CUDA(cudaMemsetAsync(fnorms, 0, sizeof(double) * P, st));
     launch_residual(m, d_omega, 0.0, Fb, nullptr, int64_t(nrhs) * n, Bdev, nrhs, rhat, int64_t(nrhs) * n, fnorms,
@@ -247,7 +251,18 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
         for (; j < mm; ++j) {
             // z_j = M^-1 v_j (low precision), back to FP64
             to_low_unit_kernel<T2><<<cdiv(int64_t(P) * n, 256), 256, 0, st>>>(V + int64_t(j) * sVb, y, int64_t(P) * n);
-            fsi_status s = solve_batch<R>(m, fc, Fb, y, int64_t(nrhs) * n, nrhs, st);
+            // solve only the frequencies that still have a live pair
+            hfl.clear();
+            for (int f = 0; f < Fb; ++f) {
+                bool any_live = false;
+                for (int cc = 0; cc < nrhs; ++cc) any_live = any_live || live[f * nrhs + cc];
+                if (any_live) hfl.push_back(f);
+            }
+            const bool sub = int(hfl.size()) < Fb;
+            if (sub)
+                GM_CUDA(cudaMemcpyAsync(flist, hfl.data(), sizeof(int32_t) * hfl.size(), cudaMemcpyHostToDevice, st));
+            fsi_status s = solve_batch<R>(m, fc, Fb, y, int64_t(nrhs) * n, nrhs, st, sub ? flist : nullptr,
+                                          int(hfl.size()));
             if (s != FSI_OK) return s;
             to_high_kernel<T2><<<cdiv(int64_t(P) * n, 256), 256, 0, st>>>(y, Z + int64_t(j) * sVb, int64_t(P) * n);
             {

@@ -144,14 +144,15 @@ void launch_cgemm_f32(float2* G, int64_t sG, int ld, int F, int r0, int r1, int 
                       cudaStream_t st);
 
 // Slab solves: per slab a triangle launch (one CTA per frequency) and a batched
-// matrix-vector launch for the off-diagonal factor blocks; tmp is unused.
+// matrix-vector launch for the off-diagonal factor blocks.  F frequencies are
+// solved: 0..F-1, or flist[0..F) when flist (device) is non-null.
 template <typename R>
 void launch_slab_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
                            const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b,
-                           int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st);
+                           int k, int nz, int nrhs, int F, const int32_t* flist, cudaStream_t st);
 template <typename R>
 void launch_slab_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY, int64_t n,
-                           int b, int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st);
+                           int b, int k, int nz, int nrhs, int F, const int32_t* flist, cudaStream_t st);
 
 // U x = B in place for the upper triangle of the first n columns; B = columns [c0, c0+nrhs).
 template <typename R>

@@ -180,11 +180,12 @@ __device__ __forceinline__ void block_rows(const T2* __restrict__ Uk, int ld, in
 template <typename T2, bool VEC, int NR>
 __global__ void __launch_bounds__(kTriThreads) tri_fwd_kernel(const T2* __restrict__ U, int64_t sU,
                                                               const int32_t* __restrict__ perm, int64_t sPerm,
-                                                              T2* y, int64_t sY, int64_t n, int b, int m) {
+                                                              T2* y, int64_t sY, int64_t n, int b, int m,
+                                                              const int32_t* __restrict__ flist) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* t = reinterpret_cast<T2*>(smem_raw);   // [NR][m]
     T2* D = t + size_t(NR) * m;                // [kTB][kTS]
-    const int f = blockIdx.x, warp = threadIdx.x >> 5;
+    const int f = flist ? flist[blockIdx.x] : blockIdx.x, warp = threadIdx.x >> 5;
     const T2* Uk = U + f * sU;
     const int32_t* pk = perm + f * sPerm;
     T2* yf = y + f * sY;
@@ -209,11 +210,12 @@ __global__ void __launch_bounds__(kTriThreads) tri_fwd_kernel(const T2* __restri
 // Backward triangle of slab k (after the far columns were subtracted), one CTA per frequency.
 template <typename T2, bool VEC, int NR>
 __global__ void __launch_bounds__(kTriThreads) tri_bwd_kernel(const T2* __restrict__ U, int64_t sU, T2* y,
-                                                              int64_t sY, int64_t n, int b) {
+                                                              int64_t sY, int64_t n, int b,
+                                                              const int32_t* __restrict__ flist) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T2* v = reinterpret_cast<T2*>(smem_raw);   // [NR][b]
     T2* D = v + size_t(NR) * b;                // [kTB][kTS]
-    const int f = blockIdx.x, warp = threadIdx.x >> 5;
+    const int f = flist ? flist[blockIdx.x] : blockIdx.x, warp = threadIdx.x >> 5;
     const T2* Uk = U + f * sU;
     T2* yf = y + f * sY;
     for (int idx = threadIdx.x; idx < b * NR; idx += blockDim.x) {
@@ -239,12 +241,13 @@ __global__ void __launch_bounds__(kTriThreads) tri_bwd_kernel(const T2* __restri
 template <typename T2, bool VEC, int NR>
 __global__ void __launch_bounds__(kGvWarps * 32, 2) slab_gemv_kernel(const T2* __restrict__ M, int64_t sM, int ldm,
                                                                   int rows, int cols, const T2* x, int64_t sX,
-                                                                  T2* out, int64_t sO, int64_t n) {
+                                                                  T2* out, int64_t sO, int64_t n,
+                                                                  const int32_t* __restrict__ flist) {
     using R = decltype(T2::x);
     using V = typename Ld<T2, VEC>::V;
     constexpr int E = Ld<T2, VEC>::E;
     constexpr int U2 = 2;   // column chunks per iteration
-    const int f = blockIdx.y;
+    const int f = flist ? flist[blockIdx.y] : blockIdx.y;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int row0 = (blockIdx.x * kGvWarps + warp) * kGvRows;
     if (row0 >= rows) return;
@@ -295,33 +298,34 @@ __global__ void __launch_bounds__(kGvWarps * 32, 2) slab_gemv_kernel(const T2* _
 
 template <typename T2, bool VEC, int NR>
 void tri_fwd(const T2* U, int64_t sU, const int32_t* perm, int64_t sPerm, T2* y, int64_t sY, int64_t n, int b, int m,
-             int F, size_t smem, cudaStream_t st) {
+             int F, const int32_t* flist, size_t smem, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tri_fwd_kernel<T2, VEC, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(kMaxSolveSmem));
         attr = true;
     }
-    tri_fwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, perm, sPerm, y, sY, n, b, m);
+    tri_fwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, perm, sPerm, y, sY, n, b, m, flist);
 }
 
 template <typename T2, bool VEC, int NR>
-void tri_bwd(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, int F, size_t smem, cudaStream_t st) {
+void tri_bwd(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, int F, const int32_t* flist, size_t smem,
+             cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tri_bwd_kernel<T2, VEC, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(kMaxSolveSmem));
         attr = true;
     }
-    tri_bwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, y, sY, n, b);
+    tri_bwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, y, sY, n, b, flist);
 }
 
 template <typename T2, bool VEC, int NR>
 void gemv(const T2* M, int64_t sM, int ldm, int rows, int cols, const T2* x, int64_t sX, T2* out, int64_t sO,
-          int64_t n, int F, cudaStream_t st) {
+          int64_t n, int F, const int32_t* flist, cudaStream_t st) {
     const int per = kGvWarps * kGvRows;
     dim3 grid((rows + per - 1) / per, F);
-    slab_gemv_kernel<T2, VEC, NR><<<grid, kGvWarps * 32, 0, st>>>(M, sM, ldm, rows, cols, x, sX, out, sO, n);
+    slab_gemv_kernel<T2, VEC, NR><<<grid, kGvWarps * 32, 0, st>>>(M, sM, ldm, rows, cols, x, sX, out, sO, n, flist);
 }
 
 // Right-hand sides per launch such that the triangle's vectors fit in shared memory.
@@ -335,7 +339,7 @@ int rhs_per_launch(int rows) {
 
 template <typename T2, bool VEC>
 void fwd_slab(const T2* U, const T2* L, int64_t sU, int64_t sL, const int32_t* perm, int64_t sPerm, T2* y,
-              int64_t sY, int64_t n, int b, int k, int nz, int nrhs, int F, cudaStream_t st) {
+              int64_t sY, int64_t n, int b, int k, int nz, int nrhs, int F, const int32_t* flist, cudaStream_t st) {
     const int m = (k + 1 < nz) ? 2 * b : b;
     const int step = rhs_per_launch<T2>(m);
     for (int c0 = 0; c0 < nrhs; c0 += step) {
@@ -345,19 +349,19 @@ void fwd_slab(const T2* U, const T2* L, int64_t sU, int64_t sL, const int32_t* p
         {
             ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(b) * b / 2.0, st);
             switch (nc) {
-                case 1: tri_fwd<T2, VEC, 1>(U, sU, perm, sPerm, yk, sY, n, b, m, F, smem, st); break;
-                case 2: tri_fwd<T2, VEC, 2>(U, sU, perm, sPerm, yk, sY, n, b, m, F, smem, st); break;
-                case 3: tri_fwd<T2, VEC, 3>(U, sU, perm, sPerm, yk, sY, n, b, m, F, smem, st); break;
-                default: tri_fwd<T2, VEC, 4>(U, sU, perm, sPerm, yk, sY, n, b, m, F, smem, st); break;
+                case 1: tri_fwd<T2, VEC, 1>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
+                case 2: tri_fwd<T2, VEC, 2>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
+                case 3: tri_fwd<T2, VEC, 3>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
+                default: tri_fwd<T2, VEC, 4>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
             }
         }
         if (m == 2 * b) {
-            ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(b) * b, st);
+            ProfScope ps(PK_GEMV, 8.0 * F * nc * double(b) * b, st);
             switch (nc) {
-                case 1: gemv<T2, VEC, 1>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, st); break;
-                case 2: gemv<T2, VEC, 2>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, st); break;
-                case 3: gemv<T2, VEC, 3>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, st); break;
-                default: gemv<T2, VEC, 4>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, st); break;
+                case 1: gemv<T2, VEC, 1>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, flist, st); break;
+                case 2: gemv<T2, VEC, 2>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, flist, st); break;
+                case 3: gemv<T2, VEC, 3>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, flist, st); break;
+                default: gemv<T2, VEC, 4>(L, sL, b, b, b, yk, sY, yk + b, sY, n, F, flist, st); break;
             }
         }
     }
@@ -365,28 +369,28 @@ void fwd_slab(const T2* U, const T2* L, int64_t sU, int64_t sL, const int32_t* p
 
 template <typename T2, bool VEC>
 void bwd_slab(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, int k, int nz, int nrhs, int F,
-              cudaStream_t st) {
+              const int32_t* flist, cudaStream_t st) {
     const int far = std::min(2, nz - 1 - k) * b;
     const int step = rhs_per_launch<T2>(b);
     for (int c0 = 0; c0 < nrhs; c0 += step) {
         const int nc = std::min(step, nrhs - c0);
         T2* yk = y + int64_t(c0) * n + int64_t(k) * b;
         if (far > 0) {
-            ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(far) * b, st);
+            ProfScope ps(PK_GEMV, 8.0 * F * nc * double(far) * b, st);
             switch (nc) {
-                case 1: gemv<T2, VEC, 1>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, st); break;
-                case 2: gemv<T2, VEC, 2>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, st); break;
-                case 3: gemv<T2, VEC, 3>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, st); break;
-                default: gemv<T2, VEC, 4>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, st); break;
+                case 1: gemv<T2, VEC, 1>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, flist, st); break;
+                case 2: gemv<T2, VEC, 2>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, flist, st); break;
+                case 3: gemv<T2, VEC, 3>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, flist, st); break;
+                default: gemv<T2, VEC, 4>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, flist, st); break;
             }
         }
         const size_t smem = (size_t(nc) * b + size_t(kTB) * kTS) * sizeof(T2);
         ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(b) * b / 2.0, st);
         switch (nc) {
-            case 1: tri_bwd<T2, VEC, 1>(U, sU, yk, sY, n, b, F, smem, st); break;
-            case 2: tri_bwd<T2, VEC, 2>(U, sU, yk, sY, n, b, F, smem, st); break;
-            case 3: tri_bwd<T2, VEC, 3>(U, sU, yk, sY, n, b, F, smem, st); break;
-            default: tri_bwd<T2, VEC, 4>(U, sU, yk, sY, n, b, F, smem, st); break;
+            case 1: tri_bwd<T2, VEC, 1>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
+            case 2: tri_bwd<T2, VEC, 2>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
+            case 3: tri_bwd<T2, VEC, 3>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
+            default: tri_bwd<T2, VEC, 4>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
         }
     }
 }
@@ -405,34 +409,32 @@ bool vec_ok(int b, const void* a, const void* c, const void* d) {
 template <typename R>
 void launch_slab_solve_fwd(const typename Cplx<R>::T* U, const typename Cplx<R>::T* L, int64_t sU, int64_t sL,
                            const int32_t* perm, int64_t sPerm, typename Cplx<R>::T* y, int64_t sY, int64_t n, int b,
-                           int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st) {
+                           int k, int nz, int nrhs, int F, const int32_t* flist, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
-    (void)tmp;
     const bool strides_even = (sU % 2 == 0) && (sL % 2 == 0) && (sY % 2 == 0) && (n % 2 == 0);
     if (strides_even && vec_ok<T2>(b, U, L, y))
-        fwd_slab<T2, true>(U, L, sU, sL, perm, sPerm, y, sY, n, b, k, nz, nrhs, F, st);
+        fwd_slab<T2, true>(U, L, sU, sL, perm, sPerm, y, sY, n, b, k, nz, nrhs, F, flist, st);
     else
-        fwd_slab<T2, false>(U, L, sU, sL, perm, sPerm, y, sY, n, b, k, nz, nrhs, F, st);
+        fwd_slab<T2, false>(U, L, sU, sL, perm, sPerm, y, sY, n, b, k, nz, nrhs, F, flist, st);
 }
 
 template <typename R>
 void launch_slab_solve_bwd(const typename Cplx<R>::T* U, int64_t sU, typename Cplx<R>::T* y, int64_t sY, int64_t n,
-                           int b, int k, int nz, int nrhs, int F, typename Cplx<R>::T* tmp, cudaStream_t st) {
+                           int b, int k, int nz, int nrhs, int F, const int32_t* flist, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
-    (void)tmp;
     const bool strides_even = (sU % 2 == 0) && (sY % 2 == 0) && (n % 2 == 0);
     if (strides_even && vec_ok<T2>(b, U, y, y))
-        bwd_slab<T2, true>(U, sU, y, sY, n, b, k, nz, nrhs, F, st);
+        bwd_slab<T2, true>(U, sU, y, sY, n, b, k, nz, nrhs, F, flist, st);
     else
-        bwd_slab<T2, false>(U, sU, y, sY, n, b, k, nz, nrhs, F, st);
+        bwd_slab<T2, false>(U, sU, y, sY, n, b, k, nz, nrhs, F, flist, st);
 }
 
 #define FSI_SOLVE_INSTANTIATE(R)                                                                                    \
     template void launch_slab_solve_fwd<R>(const Cplx<R>::T*, const Cplx<R>::T*, int64_t, int64_t, const int32_t*, \
                                            int64_t, Cplx<R>::T*, int64_t, int64_t, int, int, int, int, int,         \
-                                           Cplx<R>::T*, cudaStream_t);                                              \
+                                           const int32_t*, cudaStream_t);                                           \
     template void launch_slab_solve_bwd<R>(const Cplx<R>::T*, int64_t, Cplx<R>::T*, int64_t, int64_t, int, int,    \
-                                           int, int, int, Cplx<R>::T*, cudaStream_t);
+                                           int, int, int, const int32_t*, cudaStream_t);
 
 FSI_SOLVE_INSTANTIATE(float)
 FSI_SOLVE_INSTANTIATE(double)
