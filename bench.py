@@ -226,7 +226,9 @@ def main():
         idx = (np.arange(B) + (step * world + rank) * B) % len(freqs)
         return freqs[idx]
 
-    ws_bytes = api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers))
+    # one workspace serves the device-buffer steps and the host-buffer (e2e) steps
+    ws_bytes = max(api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers)),
+                   api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers), host_io=True))
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     kw = dict(precision=args.precision, batch=B, max_refine=60, tol=REFINE_TOL, workspace=ws, allow_noconv=True)

@@ -8,8 +8,9 @@
 // 4*ty..4*ty+3 and 64+4*ty.., columns 2*tx, 2*tx+1 and 32+2*tx, 33+2*tx), so one
 // K step costs six 16-byte shared loads for 128 FMAs.  K is staged 16 at a time
 // in two shared-memory buffers: the next slice is copied from global memory by
-// cp.async (no staging registers) while the current one is multiplied.  Two CTAs fit per SM, so
-// one CTA's epilogue (the read-modify-write of C) overlaps the other's FMAs.
+// cp.async (no staging registers) while the current one is multiplied.  Two
+// CTAs fit per SM, so one CTA's epilogue (the read-modify-write of C, whose
+// lines are prefetched into L2 when the CTA starts) overlaps the other's FMAs.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,7 +35,7 @@ __device__ __forceinline__ void cp_async8(uint32_t saddr, const void* g, bool ok
 }
 
 __global__ void __launch_bounds__(kCT, 2) cgemm_f32_kernel(float2* __restrict__ G, int64_t sG, int ld, int r0, int r1,
-                                                           int c0, int c1, int k0, int K) {
+                                                           int c0, int c1, int k0, int K, bool vec_ok) {
     __shared__ __align__(16) float2 As[2][kCK][kCM];
     __shared__ __align__(16) float2 Bs[2][kCK][kCN];
     const int f = blockIdx.z;
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(kCT, 2) cgemm_f32_kernel(float2* __restrict__ 
 
     // global -> shared copies (cp.async, zero-filled outside the block):
     // A row la_r, k in [la_k, la_k+8) stored transposed; B k row lb_k, columns [lb_c, lb_c+4)
-    const int la_r = tid >> 1, la_k = (tid & 1) * 8;
+    const int la_r = tid & (kCM - 1), la_k = (tid >> 7) * 8;   // a warp fills 32 consecutive rows of As
     const int lb_k = tid >> 4, lb_c = (tid & 15) * 4;
     const bool a_ok = rb + la_r < r1;
     const float2* a_src = A + int64_t(min(rb + la_r, r1 - 1)) * ld + k0 + la_k;
@@ -64,6 +65,19 @@ __global__ void __launch_bounds__(kCT, 2) cgemm_f32_kernel(float2* __restrict__ 
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
+
+    // the C tile is read-modify-written at the end: start pulling it into L2 now
+    {
+        const int pr = tid >> 1;
+        if (rb + pr < r1) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = cb + ((tid & 1) * 2 + h) * 16;   // 16 complex = one 128-byte line
+                if (col < c1)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"(A + int64_t(rb + pr) * ld + col));
+            }
+        }
+    }
 
     float2 acc[8][4];
 #pragma unroll
@@ -99,16 +113,32 @@ __global__ void __launch_bounds__(kCT, 2) cgemm_f32_kernel(float2* __restrict__ 
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
     }
+    // epilogue: columns 2*tx, 2*tx+1 (and 32 + those) are adjacent, so pairs move as 16 bytes
+    const bool pairs = vec_ok && cb + kCN <= c1;
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         const int row = rb + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
         if (row >= r1) continue;
+        float2* crow = A + int64_t(row) * ld + cb;
+        if (pairs) {
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int col = cb + (j < 2 ? tx * 2 + j : 32 + tx * 2 + (j - 2));
-            if (col >= c1) continue;
-            float2& c = A[int64_t(row) * ld + col];
-            c = csub(c, acc[i][j]);
+            for (int h = 0; h < 2; ++h) {
+                float4* p = reinterpret_cast<float4*>(crow + h * 32 + tx * 2);
+                float4 c = *p;
+                c.x -= acc[i][2 * h].x;
+                c.y -= acc[i][2 * h].y;
+                c.z -= acc[i][2 * h + 1].x;
+                c.w -= acc[i][2 * h + 1].y;
+                *p = c;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int col = cb + (j < 2 ? tx * 2 + j : 32 + tx * 2 + (j - 2));
+                if (col >= c1) continue;
+                float2& c = A[int64_t(row) * ld + col];
+                c = csub(c, acc[i][j]);
+            }
         }
     }
 }
@@ -120,7 +150,10 @@ void launch_cgemm_f32(float2* G, int64_t sG, int ld, int F, int r0, int r1, int 
     if (r1 <= r0 || c1 <= c0 || K <= 0) return;
     dim3 grid(unsigned((c1 - c0 + kCN - 1) / kCN), unsigned((r1 - r0 + kCM - 1) / kCM), unsigned(F));
     ProfScope ps(PK_GEMM, 8.0 * F * double(r1 - r0) * double(c1 - c0) * K, st);
-    cgemm_f32_kernel<<<grid, kCT, 0, st>>>(G, sG, ld, r0, r1, c0, c1, k0, K);
+    // 16-byte epilogue access needs every tile's first column and every row start 16-byte aligned
+    const bool vec_ok = ((reinterpret_cast<uintptr_t>(G) & 15) == 0) && (ld % 2 == 0) && (c0 % 2 == 0) &&
+                        (sG % 2 == 0);
+    cgemm_f32_kernel<<<grid, kCT, 0, st>>>(G, sG, ld, r0, r1, c0, c1, k0, K, vec_ok);
 }
 
 }  // namespace fsi

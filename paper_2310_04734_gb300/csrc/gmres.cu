@@ -42,54 +42,82 @@ constexpr int kGChunks = 32;
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
-// w_p = A^ z_p = rs o (A(w_f) (cs o z_p))   for active pairs
-__global__ void apply_kernel(DevModel m, const double* omega, const double2* z, double2* w, int nrhs,
-                             const int32_t* active) {
-    const int p = blockIdx.y;
-    if (active && !active[p]) return;
-    const int f = p / nrhs;
+constexpr int kApR = 8;    // load columns per thread in the operator application
+constexpr int kGrV = 8;    // basis vectors per pass of the Gram kernel
+
+// w_p = A^ z_p = rs o (A(w_f) (cs o z_p)) for the active pairs p = f*nrhs + c0 + c,
+// c < nc <= kApR: one thread per (row, frequency) forms each scaled entry once and
+// applies it to every load column, so the matrix is streamed once per frequency.
+__global__ void apply_kernel(DevModel m, const double* omega, const double2* z, double2* w, int nrhs, int c0,
+                             int nc, const int32_t* active) {
+    const int f = blockIdx.y;
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= m.n) return;
+    const int p0 = f * nrhs + c0;
+    bool any = false;
+#pragma unroll
+    for (int c = 0; c < kApR; ++c)
+        if (c < nc) any = any || !active || active[p0 + c];
+    if (!any) return;
     const double om = omega[f];
-    const double2* zp = z + int64_t(p) * m.n;
-    double2 acc = make_double2(0.0, 0.0);
+    double2 acc[kApR];
+#pragma unroll
+    for (int c = 0; c < kApR; ++c) acc[c] = make_double2(0.0, 0.0);
     for (int e = m.rowptr[i]; e < m.rowptr[i + 1]; ++e) {
         const int64_t col = m.col[e];
         double2 a = a_entry(m, e, om);
         const double s = col_scale(m, col, om);
         a.x *= s;
         a.y *= s;
-        cfma(acc, a, zp[col]);
+#pragma unroll
+        for (int c = 0; c < kApR; ++c)
+            if (c < nc) cfma(acc[c], a, z[int64_t(p0 + c) * m.n + col]);
     }
     const double rs = row_scale(m, i, om);
-    w[int64_t(p) * m.n + i] = make_double2(rs * acc.x, rs * acc.y);
+#pragma unroll
+    for (int c = 0; c < kApR; ++c)
+        if (c < nc && (!active || active[p0 + c]))
+            w[int64_t(p0 + c) * m.n + i] = make_double2(rs * acc[c].x, rs * acc[c].y);
 }
 
-// partial[chunk][p][i] = sum_{n in chunk} conj(V_i[p][n]) w[p][n],  i < nv
-__global__ void bgram_partial_kernel(const double2* V, int64_t sVb, int64_t n, int nv, const double2* w,
-                                     double2* partial, int P, const int32_t* active) {
-    const int i = blockIdx.x, p = blockIdx.y, ch = blockIdx.z;
+// partial[chunk][p][i0 + i] = sum_{q in chunk} conj(V_{i0+i}[p][q]) w[p][q],  i < ni <= kGrV;
+// w is read once per pass for all ni basis vectors
+__global__ void bgram_partial_kernel(const double2* V, int64_t sVb, int64_t n, int nv, int i0, int ni,
+                                     const double2* w, double2* partial, int P, const int32_t* active) {
+    const int p = blockIdx.x, ch = blockIdx.y;
     if (active && !active[p]) return;
     const int64_t len = (n + kGChunks - 1) / kGChunks;
     const int64_t a = ch * len, b = min(n, a + len);
-    const double2* v = V + int64_t(i) * sVb + int64_t(p) * n;
     const double2* wp = w + int64_t(p) * n;
-    double2 acc = make_double2(0.0, 0.0);
+    double2 acc[kGrV];
+#pragma unroll
+    for (int i = 0; i < kGrV; ++i) acc[i] = make_double2(0.0, 0.0);
     for (int64_t q = a + threadIdx.x; q < b; q += blockDim.x) {
-        const double2 x = v[q];
-        cfma(acc, make_double2(x.x, -x.y), wp[q]);
+        const double2 wv = wp[q];
+#pragma unroll
+        for (int i = 0; i < kGrV; ++i)
+            if (i < ni) {
+                const double2 x = V[int64_t(i0 + i) * sVb + int64_t(p) * n + q];
+                cfma(acc[i], make_double2(x.x, -x.y), wv);
+            }
     }
-    __shared__ double2 red[32];
-    for (int off = 16; off > 0; off >>= 1) {
-        acc.x += __shfl_down_sync(0xffffffffu, acc.x, off);
-        acc.y += __shfl_down_sync(0xffffffffu, acc.y, off);
+    __shared__ double2 red[kGrV][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < kGrV; ++i) {
+        if (i >= ni) break;
+        double2 v = acc[i];
+        for (int off = 16; off > 0; off >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) red[i][warp] = v;
     }
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double2 s = make_double2(0.0, 0.0);
-        for (int q = 0; q < int(blockDim.x >> 5); ++q) s = cadd(s, red[q]);
-        partial[(int64_t(ch) * P + p) * nv + i] = s;
+    if (threadIdx.x < ni) {
+        double2 s2 = make_double2(0.0, 0.0);
+        for (int q = 0; q < int(blockDim.x >> 5); ++q) s2 = cadd(s2, red[threadIdx.x][q]);
+        partial[(int64_t(ch) * P + p) * nv + i0 + threadIdx.x] = s2;
     }
 }
 
@@ -267,12 +295,17 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
             to_high_kernel<T2><<<cdiv(int64_t(P) * n, 256), 256, 0, st>>>(y, Z + int64_t(j) * sVb, int64_t(P) * n);
             {
                 ProfScope ps(PK_RESID, 0.0, st);
-                apply_kernel<<<dim3(cdiv(n, 256), P), 256, 0, st>>>(m, d_omega, Z + int64_t(j) * sVb, w, nrhs, act);
+                for (int c0 = 0; c0 < nrhs; c0 += kApR)
+                    apply_kernel<<<dim3(cdiv(n, 256), Fb), 256, 0, st>>>(m, d_omega, Z + int64_t(j) * sVb, w, nrhs,
+                                                                         c0, std::min(kApR, nrhs - c0), act);
             }
             // CGS2 against v_0..v_j
             for (int pass = 0; pass < 2; ++pass) {
                 ProfScope ps(PK_RESID, 0.0, st);
-                bgram_partial_kernel<<<dim3(j + 1, P, kGChunks), 256, 0, st>>>(V, sVb, n, j + 1, w, part, P, act);
+                for (int i0 = 0; i0 <= j; i0 += kGrV)
+                    bgram_partial_kernel<<<dim3(P, kGChunks), 256, 0, st>>>(V, sVb, n, j + 1, i0,
+                                                                            std::min(kGrV, j + 1 - i0), w, part, P,
+                                                                            act);
                 bgram_reduce_kernel<<<cdiv(int64_t(P) * (j + 1), 256), 256, 0, st>>>(part, P, j + 1, yd);
                 GM_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * P, st));
                 bupdate_kernel<<<dim3(cdiv(n, 256), P), 256, 0, st>>>(V, sVb, n, j + 1, yd, w, nrm, act);

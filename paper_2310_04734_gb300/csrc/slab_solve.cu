@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_fwd_kernel(const T2* __restri
     const int f = flist ? flist[blockIdx.x] : blockIdx.x, warp = threadIdx.x >> 5;
     const T2* Uk = U + f * sU;
     const int32_t* pk = perm + f * sPerm;
-    T2* yf = y + f * sY;
+    T2* yf = y + f * sY + int64_t(blockIdx.y) * NR * n;   // this CTA's right-hand sides
     for (int idx = threadIdx.x; idx < m * NR; idx += blockDim.x) {
         const int c = idx / m, i = idx - c * m;
         t[c * m + i] = yf[c * n + pk[i]];
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kTriThreads) tri_bwd_kernel(const T2* __restri
     T2* D = v + size_t(NR) * b;                // [kTB][kTS]
     const int f = flist ? flist[blockIdx.x] : blockIdx.x, warp = threadIdx.x >> 5;
     const T2* Uk = U + f * sU;
-    T2* yf = y + f * sY;
+    T2* yf = y + f * sY + int64_t(blockIdx.y) * NR * n;   // this CTA's right-hand sides
     for (int idx = threadIdx.x; idx < b * NR; idx += blockDim.x) {
         const int c = idx / b, i = idx - c * b;
         v[c * b + i] = yf[c * n + i];
@@ -298,26 +298,26 @@ __global__ void __launch_bounds__(kGvWarps * 32, 2) slab_gemv_kernel(const T2* _
 
 template <typename T2, bool VEC, int NR>
 void tri_fwd(const T2* U, int64_t sU, const int32_t* perm, int64_t sPerm, T2* y, int64_t sY, int64_t n, int b, int m,
-             int F, const int32_t* flist, size_t smem, cudaStream_t st) {
+             dim3 grid, const int32_t* flist, size_t smem, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tri_fwd_kernel<T2, VEC, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(kMaxSolveSmem));
         attr = true;
     }
-    tri_fwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, perm, sPerm, y, sY, n, b, m, flist);
+    tri_fwd_kernel<T2, VEC, NR><<<grid, kTriThreads, smem, st>>>(U, sU, perm, sPerm, y, sY, n, b, m, flist);
 }
 
 template <typename T2, bool VEC, int NR>
-void tri_bwd(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, int F, const int32_t* flist, size_t smem,
-             cudaStream_t st) {
+void tri_bwd(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, dim3 grid, const int32_t* flist,
+             size_t smem, cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tri_bwd_kernel<T2, VEC, NR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              int(kMaxSolveSmem));
         attr = true;
     }
-    tri_bwd_kernel<T2, VEC, NR><<<F, kTriThreads, smem, st>>>(U, sU, y, sY, n, b, flist);
+    tri_bwd_kernel<T2, VEC, NR><<<grid, kTriThreads, smem, st>>>(U, sU, y, sY, n, b, flist);
 }
 
 template <typename T2, bool VEC, int NR>
@@ -326,6 +326,23 @@ void gemv(const T2* M, int64_t sM, int ldm, int rows, int cols, const T2* x, int
     const int per = kGvWarps * kGvRows;
     dim3 grid((rows + per - 1) / per, F);
     slab_gemv_kernel<T2, VEC, NR><<<grid, kGvWarps * 32, 0, st>>>(M, sM, ldm, rows, cols, x, sX, out, sO, n, flist);
+}
+
+// Right-hand sides per triangle CTA.  The triangle of one frequency is a chain of
+// dependent block steps on one SM, issue-bound on its FMAs, so the right-hand sides
+// are spread over CTAs (each rereads the triangle, mostly from L2) while the grid
+// still fits on the SMs at once.
+int tri_rhs_per_cta(int F, int nc) {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    for (int nr : {1, 2, 4})
+        if (nc % nr == 0 && int64_t(F) * (nc / nr) <= sms) return nr;
+    return nc % 4 == 0 ? 4 : (nc % 2 == 0 ? 2 : 1);
 }
 
 // Right-hand sides per launch such that the triangle's vectors fit in shared memory.
@@ -345,14 +362,15 @@ void fwd_slab(const T2* U, const T2* L, int64_t sU, int64_t sL, const int32_t* p
     for (int c0 = 0; c0 < nrhs; c0 += step) {
         const int nc = std::min(step, nrhs - c0);
         T2* yk = y + int64_t(c0) * n + int64_t(k) * b;
-        const size_t smem = (size_t(nc) * m + size_t(kTB) * kTS) * sizeof(T2);
         {
+            const int nr = tri_rhs_per_cta(F, nc);
+            const dim3 grid(unsigned(F), unsigned(nc / nr));
+            const size_t smem = (size_t(nr) * m + size_t(kTB) * kTS) * sizeof(T2);
             ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(b) * b / 2.0, st);
-            switch (nc) {
-                case 1: tri_fwd<T2, VEC, 1>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
-                case 2: tri_fwd<T2, VEC, 2>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
-                case 3: tri_fwd<T2, VEC, 3>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
-                default: tri_fwd<T2, VEC, 4>(U, sU, perm, sPerm, yk, sY, n, b, m, F, flist, smem, st); break;
+            switch (nr) {
+                case 1: tri_fwd<T2, VEC, 1>(U, sU, perm, sPerm, yk, sY, n, b, m, grid, flist, smem, st); break;
+                case 2: tri_fwd<T2, VEC, 2>(U, sU, perm, sPerm, yk, sY, n, b, m, grid, flist, smem, st); break;
+                default: tri_fwd<T2, VEC, 4>(U, sU, perm, sPerm, yk, sY, n, b, m, grid, flist, smem, st); break;
             }
         }
         if (m == 2 * b) {
@@ -384,13 +402,14 @@ void bwd_slab(const T2* U, int64_t sU, T2* y, int64_t sY, int64_t n, int b, int 
                 default: gemv<T2, VEC, 4>(U + b, sU, 3 * b, b, far, yk + b, sY, yk, sY, n, F, flist, st); break;
             }
         }
-        const size_t smem = (size_t(nc) * b + size_t(kTB) * kTS) * sizeof(T2);
+        const int nr = tri_rhs_per_cta(F, nc);
+        const dim3 grid(unsigned(F), unsigned(nc / nr));
+        const size_t smem = (size_t(nr) * b + size_t(kTB) * kTS) * sizeof(T2);
         ProfScope ps(PK_SOLVE, 8.0 * F * nc * double(b) * b / 2.0, st);
-        switch (nc) {
-            case 1: tri_bwd<T2, VEC, 1>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
-            case 2: tri_bwd<T2, VEC, 2>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
-            case 3: tri_bwd<T2, VEC, 3>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
-            default: tri_bwd<T2, VEC, 4>(U, sU, yk, sY, n, b, F, flist, smem, st); break;
+        switch (nr) {
+            case 1: tri_bwd<T2, VEC, 1>(U, sU, yk, sY, n, b, grid, flist, smem, st); break;
+            case 2: tri_bwd<T2, VEC, 2>(U, sU, yk, sY, n, b, grid, flist, smem, st); break;
+            default: tri_bwd<T2, VEC, 4>(U, sU, yk, sY, n, b, grid, flist, smem, st); break;
         }
     }
 }
