@@ -268,6 +268,78 @@ fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64*
                      const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
                      fsi_c64* p_out, double* spl_out, void* stream);
 
+/* Greedy expansion points (paper Sec. 3.3; its error measure replaced by a
+ * residual estimate, as Sec. 5 suggests).  Options: */
+typedef struct {
+    int q;                        /* moments per load column per expansion point   */
+    int kmax;                     /* basis columns at most (<= 1024)               */
+    int max_shifts;               /* expansion points at most (initial included)  */
+    double tol;                   /* stop when the largest estimate is <= tol      */
+    fsi_rom_opts build;           /* factor precision / refinement of the moments */
+} fsi_greedy_opts;
+
+/* Workspace bytes for rom_greedy (includes one rom_build workspace). */
+fsi_status rom_greedy_workspace(const fsi_dims* dims, int nrhs, const fsi_greedy_opts* opts, size_t* bytes);
+
+/* Builds the rational Arnoldi basis from init_hz (ninit points; 0: the middle
+ * candidate), then repeatedly: projects (Galerkin, as rom_project), evaluates
+ * at every candidate frequency the residual estimate
+ *   est(w) = |R(w)(F - A(w) V x_R(w))|_F / |R(w) F|_F
+ * (R(w): the full-order sweep's row equilibration; x_R: the reduced solution)
+ * exactly from FP64 Gram blocks of [KV, DV, MV], and stops when max est <= tol,
+ * at max_shifts points or at kmax columns; otherwise adds the candidate of
+ * largest estimate (ties: lowest frequency) more than one candidate step away
+ * from every existing point and appends its moments.  Candidates: host,
+ * positive, strictly increasing.  F, V (n x kmax), KR/DR/MR (kmax x kmax
+ * buffers; on return k x k, ld k), fR (k x nrhs, ld k), rcv, CR (nrcv x k):
+ * device, column-major; rcv/CR may be NULL.  Host outputs: shifts_out
+ * (max_shifts), *nshift_out, est_out (ncand; last estimates; nullable),
+ * hist_out (max_shifts; largest estimate per round; nullable).  Errors:
+ * FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA, FSI_ESINGULAR. */
+fsi_status rom_greedy(const fsi_dims* dims, const void* d_model, const fsi_c64* F, int nrhs,
+                      const double* cand_hz, int ncand, const double* init_hz, int ninit,
+                      const fsi_greedy_opts* opts, void* ws, size_t ws_bytes, fsi_c64* V, int* k_out,
+                      fsi_c64* KR, fsi_c64* DR, fsi_c64* MR, fsi_c64* fR, const int32_t* rcv, int nrcv,
+                      fsi_c64* CR, double* shifts_out, int* nshift_out, double* est_out, double* hist_out,
+                      void* stream);
+
+/* Local ROM windows (paper Sec. 3.3: one fROM per frequency window).  The
+ * candidate band starts as one window with its own rom_greedy (initial points
+ * at the window's quarter midpoints); a window whose greedy stops with its
+ * largest estimate above greedy.tol is bisected (by candidate count), down to
+ * min_points candidates, at most max_windows windows in all. */
+typedef struct {
+    fsi_greedy_opts greedy;       /* per window                                     */
+    int max_windows;
+    int min_points;               /* a window is not split below this many points  */
+} fsi_window_opts;
+
+/* Workspace bytes for rom_windows (one greedy workspace + an n x kmax basis). */
+fsi_status rom_windows_workspace(const fsi_dims* dims, int nrhs, const fsi_window_opts* opts, size_t* bytes);
+
+/* Windows in increasing frequency order.  Device outputs, slot w of each:
+ * KR/DR/MR at w*kmax*kmax (k_w x k_w, ld k_w), fR at w*kmax*nrhs (k_w x nrhs),
+ * CR at w*nrcv*kmax (nrcv x k_w); buffers hold max_windows slots.  Host
+ * outputs (max_windows entries): window [lo, hi] (first and last candidate),
+ * k, number of expansion points, largest final estimate.  Errors as rom_greedy. */
+fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64* F, int nrhs,
+                       const double* cand_hz, int ncand, const fsi_window_opts* opts, void* ws,
+                       size_t ws_bytes, const int32_t* rcv, int nrcv, fsi_c64* KR, fsi_c64* DR,
+                       fsi_c64* MR, fsi_c64* fR, fsi_c64* CR, int* nwin_out, double* lo_out,
+                       double* hi_out, int* k_out, int* nshift_out, double* maxest_out, void* stream);
+
+/* Workspace bytes for rom_windows_sweep. */
+fsi_status rom_windows_sweep_workspace(int kmax, int nrhs, int batch, size_t* bytes);
+
+/* Reduced sweep with windowed ROMs (layout of rom_windows): every frequency is
+ * solved with the window that contains it, else the nearer neighbour.
+ * f_hz host, increasing; p_out/spl_out as rom_sweep. */
+fsi_status rom_windows_sweep(int nwin, const double* lo, const double* hi, const int* k, int kmax,
+                             const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR,
+                             const fsi_c64* fR, const fsi_c64* CR, int nrhs, int nrcv,
+                             const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
+                             fsi_c64* p_out, double* spl_out, void* stream);
+
 const char* fsi_status_str(fsi_status s);
 const char* fsi_last_error(void);
 

@@ -208,3 +208,35 @@ def greedy(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts:
         shifts.append(nxt)
         V = build_basis(asm, [nxt], q, F, kmax, V0=V)
     return shifts, V, project(asm, V, F, rcv_dofs), history
+
+
+def windows(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts: int,
+            max_windows: int, min_points: int):
+    """Local ROMs over frequency windows (Sec. 3.3: one fROM per window).
+
+    The candidate band starts as one window; each window gets its own greedy
+    ROM started from the candidates nearest its quarter midpoints.  A window
+    whose greedy ends with its largest estimate above tol is bisected by
+    candidate count (left half first), down to min_points candidates and at
+    most max_windows windows in all.
+    """
+    cand_hz = np.asarray(cand_hz, dtype=float)
+    todo = [(0, len(cand_hz))]
+    out = []
+    while todo:
+        i0, i1 = todo.pop(0)
+        c = cand_hz[i0:i1]
+        init = []
+        for qq in range(4):
+            t = c[0] + (c[-1] - c[0]) * (qq + 0.5) / 4.0
+            pick = float(c[int(np.argmin(np.abs(c - t)))])
+            if pick not in init and len(init) < max_shifts:
+                init.append(pick)
+        shifts, V, rm, hist = greedy(asm, F, rcv_dofs, c, q, kmax, tol, max_shifts, initial_hz=init)
+        mx = hist[-1]
+        if mx > tol and (i1 - i0) >= 2 * max(1, min_points) and len(out) + len(todo) + 2 <= max_windows:
+            mid = i0 + (i1 - i0) // 2
+            todo[0:0] = [(i0, mid), (mid, i1)]
+            continue
+        out.append(dict(lo=float(c[0]), hi=float(c[-1]), shifts=shifts, V=V, rm=rm, maxest=mx))
+    return out

@@ -52,6 +52,15 @@ class fsi_rom_opts(C.Structure):
                 ("second_order", c_int)]
 
 
+class fsi_greedy_opts(C.Structure):
+    _fields_ = [("q", c_int), ("kmax", c_int), ("max_shifts", c_int), ("tol", C.c_double),
+                ("build", fsi_rom_opts)]
+
+
+class fsi_window_opts(C.Structure):
+    _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "fsi_model_dims": (c_int, [C.POINTER(fsi_model_desc), C.POINTER(fsi_dims)]),
@@ -82,6 +91,22 @@ SIGNATURES = {
     "rom_sweep_workspace": (c_int, [c_int, c_int, c_int, c_int, C.POINTER(c_size_t)]),
     "rom_sweep": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
                           c_double_p, c_int, c_int, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    "rom_greedy_workspace": (c_int, [C.POINTER(fsi_dims), c_int, C.POINTER(fsi_greedy_opts),
+                                     C.POINTER(c_size_t)]),
+    "rom_greedy": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_double_p, c_int, c_double_p,
+                           c_int, C.POINTER(fsi_greedy_opts), c_void_p, c_size_t, c_void_p, C.POINTER(c_int),
+                           c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_double_p,
+                           C.POINTER(c_int), c_double_p, c_double_p, c_void_p]),
+    "rom_windows_workspace": (c_int, [C.POINTER(fsi_dims), c_int, C.POINTER(fsi_window_opts),
+                                      C.POINTER(c_size_t)]),
+    "rom_windows": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_double_p, c_int,
+                            C.POINTER(fsi_window_opts), c_void_p, c_size_t, c_void_p, c_int, c_void_p, c_void_p,
+                            c_void_p, c_void_p, c_void_p, C.POINTER(c_int), c_double_p, c_double_p, c_int32_p,
+                            c_int32_p, c_double_p, c_void_p]),
+    "rom_windows_sweep_workspace": (c_int, [c_int, c_int, c_int, C.POINTER(c_size_t)]),
+    "rom_windows_sweep": (c_int, [c_int, c_double_p, c_double_p, c_int32_p, c_int, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_int, c_int, c_double_p, c_int, c_int, c_void_p, c_size_t,
+                                  c_void_p, c_void_p, c_void_p]),
     "fsi_status_str": (C.c_char_p, [c_int]),
     "fsi_last_error": (C.c_char_p, []),
 }

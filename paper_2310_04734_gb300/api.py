@@ -324,6 +324,135 @@ def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256):
     return p, spl
 
 
+@dataclass
+class GreedyResult:
+    V: object            # n x k basis (torch, device)
+    rom: DeviceROM
+    shifts_hz: np.ndarray
+    est: np.ndarray      # residual estimate at every candidate (last round)
+    history: np.ndarray  # largest estimate per round
+
+
+def rom_greedy(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
+               init_hz=None, precision="fp32_ir", max_refine=10, refine_tol=1e-10,
+               second_order=-1) -> GreedyResult:
+    """Greedy expansion points with the Gram-block residual estimate (C-ABI rom_greedy)."""
+    torch = _torch()
+    lib = L.load()
+    cand = np.ascontiguousarray(np.asarray(cand_hz, dtype=np.float64))
+    init = np.ascontiguousarray(np.asarray([] if init_hz is None else init_hz, dtype=np.float64))
+    n = int(model.dims.n)
+    nrhs = F.shape[1]
+    o = L.fsi_greedy_opts()
+    o.q, o.kmax, o.max_shifts, o.tol = int(q), int(kmax), int(max_shifts), float(tol)
+    o.build = _rom_opts(precision, max_refine, refine_tol, second_order)
+    need = C.c_size_t()
+    L.check(lib.rom_greedy_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_greedy_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    Fc = F.t().contiguous()
+    r = rcv.to(torch.int32).contiguous()
+    nrcv = int(r.numel())
+    Vt = torch.zeros((kmax, n), dtype=torch.complex128, device="cuda")
+    KR = torch.empty(kmax * kmax, dtype=torch.complex128, device="cuda")
+    DR = torch.empty_like(KR)
+    MR = torch.empty_like(KR)
+    fR = torch.empty(kmax * nrhs, dtype=torch.complex128, device="cuda")
+    CR = torch.empty(kmax * nrcv, dtype=torch.complex128, device="cuda")
+    k = C.c_int(0)
+    ns = C.c_int(0)
+    shifts = np.zeros(max_shifts, np.float64)
+    est = np.zeros(cand.size, np.float64)
+    hist = np.zeros(max_shifts, np.float64)
+    L.check(lib.rom_greedy(C.byref(model.dims), _ptr(model.buf), _ptr(Fc), nrhs, cand.ctypes.data_as(L.c_double_p),
+                           int(cand.size), init.ctypes.data_as(L.c_double_p), int(init.size), C.byref(o), _ptr(ws),
+                           C.c_size_t(need.value), _ptr(Vt), C.byref(k), _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR),
+                           _ptr(r), nrcv, _ptr(CR), shifts.ctypes.data_as(L.c_double_p), C.byref(ns),
+                           est.ctypes.data_as(L.c_double_p), hist.ctypes.data_as(L.c_double_p), _stream_ptr()),
+            "rom_greedy")
+    kk, nsh = k.value, ns.value
+    cm = lambda buf, r_, c_: buf[:r_ * c_].view(c_, r_).t()   # column-major r_ x c_ buffer as a matrix
+    rom = DeviceROM(KR=cm(KR, kk, kk), DR=cm(DR, kk, kk), MR=cm(MR, kk, kk), fR=cm(fR, kk, nrhs),
+                    CR=cm(CR, nrcv, kk))
+    nrounds = nsh - max(int(init.size), 1) + 1
+    return GreedyResult(V=Vt[:kk].t(), rom=rom, shifts_hz=shifts[:nsh].copy(), est=est,
+                        history=hist[:max(nrounds, 0)].copy())
+
+
+@dataclass
+class WindowedROM:
+    lo: np.ndarray        # first candidate of each window (Hz)
+    hi: np.ndarray        # last candidate of each window
+    k: np.ndarray         # basis columns per window
+    nshift: np.ndarray    # expansion points per window
+    maxest: np.ndarray    # largest final residual estimate per window
+    kmax: int
+    nrhs: int
+    nrcv: int
+    bufs: tuple           # device slots (KR, DR, MR, fR, CR)
+
+
+def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
+                max_windows: int = 16, min_points: int = 4, precision="fp32_ir", max_refine=10,
+                refine_tol=1e-10, second_order=-1) -> WindowedROM:
+    """Local ROMs over windows of the candidate band (C-ABI rom_windows)."""
+    torch = _torch()
+    lib = L.load()
+    cand = np.ascontiguousarray(np.asarray(cand_hz, dtype=np.float64))
+    nrhs = F.shape[1]
+    o = L.fsi_window_opts()
+    o.greedy.q, o.greedy.kmax, o.greedy.max_shifts, o.greedy.tol = int(q), int(kmax), int(max_shifts), float(tol)
+    o.greedy.build = _rom_opts(precision, max_refine, refine_tol, second_order)
+    o.max_windows, o.min_points = int(max_windows), int(min_points)
+    need = C.c_size_t()
+    L.check(lib.rom_windows_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_windows_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    Fc = F.t().contiguous()
+    r = rcv.to(torch.int32).contiguous()
+    nrcv = int(r.numel())
+    W = int(max_windows)
+    KR = torch.empty(W * kmax * kmax, dtype=torch.complex128, device="cuda")
+    DR = torch.empty_like(KR)
+    MR = torch.empty_like(KR)
+    fR = torch.empty(W * kmax * nrhs, dtype=torch.complex128, device="cuda")
+    CR = torch.empty(W * nrcv * kmax, dtype=torch.complex128, device="cuda")
+    nw = C.c_int(0)
+    lo, hi, mx = np.zeros(W), np.zeros(W), np.zeros(W)
+    kk, ns = np.zeros(W, np.int32), np.zeros(W, np.int32)
+    L.check(lib.rom_windows(C.byref(model.dims), _ptr(model.buf), _ptr(Fc), nrhs, cand.ctypes.data_as(L.c_double_p),
+                            int(cand.size), C.byref(o), _ptr(ws), C.c_size_t(need.value), _ptr(r), nrcv, _ptr(KR),
+                            _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR), C.byref(nw), lo.ctypes.data_as(L.c_double_p),
+                            hi.ctypes.data_as(L.c_double_p), kk.ctypes.data_as(L.c_int32_p),
+                            ns.ctypes.data_as(L.c_int32_p), mx.ctypes.data_as(L.c_double_p), _stream_ptr()),
+            "rom_windows")
+    n = nw.value
+    del ws
+    return WindowedROM(lo=lo[:n].copy(), hi=hi[:n].copy(), k=kk[:n].copy(), nshift=ns[:n].copy(),
+                       maxest=mx[:n].copy(), kmax=int(kmax), nrhs=nrhs, nrcv=nrcv, bufs=(KR, DR, MR, fR, CR))
+
+
+def rom_windows_sweep(wr: WindowedROM, freqs_hz, batch: int = 256):
+    """Receiver pressures and SPL [nf][nrcv][nrhs] from windowed ROMs (torch, device)."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    bt = min(batch, nf)
+    need = C.c_size_t()
+    L.check(lib.rom_windows_sweep_workspace(wr.kmax, wr.nrhs, bt, C.byref(need)), "rom_windows_sweep_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    p = torch.empty((nf, wr.nrcv, wr.nrhs), dtype=torch.complex128, device="cuda")
+    spl = torch.empty((nf, wr.nrcv, wr.nrhs), dtype=torch.float64, device="cuda")
+    lo = np.ascontiguousarray(wr.lo)
+    hi = np.ascontiguousarray(wr.hi)
+    k = np.ascontiguousarray(wr.k.astype(np.int32))
+    KR, DR, MR, fR, CR = wr.bufs
+    L.check(lib.rom_windows_sweep(len(k), lo.ctypes.data_as(L.c_double_p), hi.ctypes.data_as(L.c_double_p),
+                                  k.ctypes.data_as(L.c_int32_p), wr.kmax, _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR),
+                                  _ptr(CR), wr.nrhs, wr.nrcv, f.ctypes.data_as(L.c_double_p), nf, bt, _ptr(ws),
+                                  C.c_size_t(need.value), _ptr(p), _ptr(spl), _stream_ptr()), "rom_windows_sweep")
+    return p, spl
+
+
 def load_matrix_dofs(spec, loads, n_rhs):
     """Load columns as (DoF index, column, value) triplets for the slab-major numbering."""
     npl = spec.nx * spec.ny

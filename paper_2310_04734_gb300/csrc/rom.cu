@@ -26,6 +26,7 @@
 #include "engine.h"
 #include "fsi_internal.h"
 #include "kernels.cuh"
+#include "rom_internal.h"
 
 namespace fsi {
 
@@ -426,7 +427,7 @@ fsi_status shifted_solve(const DevModel& m, RomWS<R>& w, double om, const double
 template <typename R>
 fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* shifts, int nshift, int q,
                          const double2* F, int nrhs, int kmax, const fsi_rom_opts& o, void* ws, size_t ws_bytes,
-                         double2* V, int* k_out, cudaStream_t st) {
+                         double2* V, int k_in, int* k_out, cudaStream_t st) {
     Carver c(ws, ws_bytes);
     RomWS<R> w;
     w.carve(c, d, nrhs, q, kmax);
@@ -454,7 +455,7 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
     } else {
         second = o.second_order != 0;
     }
-    int k = 0;
+    int k = k_in;   // columns already in V (orthonormal)
     std::vector<int32_t> hstat(1);
     for (int sidx = 0; sidx < nshift && k < kmax; ++sidx) {
         const double om = 2.0 * M_PI * shifts[sidx];
@@ -553,6 +554,85 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
 
 }  // namespace
 
+template <typename R>
+size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax) {
+    return rom_ws_bytes<R>(d, nrhs, q, kmax);
+}
+
+template <typename R>
+fsi_status rom_build_append(const fsi_dims& d, const void* d_model, const double* shifts, int nshift, int q,
+                            const double2* F, int nrhs, int kmax, const fsi_rom_opts& o, void* ws, size_t ws_bytes,
+                            double2* V, int k_in, int* k_out, cudaStream_t st) {
+    return run_rom_build<R>(d, d_model, shifts, nshift, q, F, nrhs, kmax, o, ws, ws_bytes, V, k_in, k_out, st);
+}
+
+template size_t rom_build_ws<float>(const fsi_dims&, int, int, int);
+template size_t rom_build_ws<double>(const fsi_dims&, int, int, int);
+template fsi_status rom_build_append<float>(const fsi_dims&, const void*, const double*, int, int, const double2*, int,
+                                            int, const fsi_rom_opts&, void*, size_t, double2*, int, int*,
+                                            cudaStream_t);
+template fsi_status rom_build_append<double>(const fsi_dims&, const void*, const double*, int, int, const double2*,
+                                             int, int, const fsi_rom_opts&, void*, size_t, double2*, int, int*,
+                                             cudaStream_t);
+
+fsi_status reduced_receivers(const ReducedBatch& rb, const double2* CR, int nrcv, double2* p, double* spl,
+                             cudaStream_t st) {
+    reduced_receivers_kernel<<<dim3(cdiv(int64_t(nrcv) * rb.nrhs, 128), rb.F), 128, 0, st>>>(rb.G, rb.k, rb.nrhs, rb.cs,
+                                                                                         CR, nrcv, p, spl);
+    ROM_LAUNCH();
+    return FSI_OK;
+}
+
+size_t reduced_solve_ws(int k, int nrhs, int batch) {
+    Carver c(nullptr, 0);
+    c.take<double2>(size_t(batch) * k * (k + nrhs));
+    c.take<int32_t>(size_t(batch) * k);
+    c.take<int32_t>(batch);
+    c.take<double>(size_t(batch) * k);
+    c.take<double>(batch);
+    return align_up(c.used);
+}
+
+fsi_status reduced_solve_batch(int k, const double2* KR, const double2* DR, const double2* MR, const double2* fR,
+                               int nrhs, const double* f_hz, int Fb, void* ws, size_t ws_bytes, ReducedBatch& out,
+                               cudaStream_t st) {
+    Carver c(ws, ws_bytes);
+    out.G = c.take<double2>(size_t(Fb) * k * (k + nrhs));
+    int32_t* ipiv = c.take<int32_t>(size_t(Fb) * k);
+    int32_t* status = c.take<int32_t>(Fb);
+    out.cs = c.take<double>(size_t(Fb) * k);
+    out.omega = c.take<double>(Fb);
+    if (!c.fits()) {
+        set_error("reduced solve workspace too small");
+        return FSI_ENOMEM;
+    }
+    out.k = k;
+    out.nrhs = nrhs;
+    out.F = Fb;
+    const int ld = k + nrhs;
+    std::vector<double> om(Fb);
+    std::vector<int32_t> hs(Fb);
+    for (int i = 0; i < Fb; ++i) om[i] = 2.0 * M_PI * f_hz[i];
+    ROM_CUDA(cudaMemcpyAsync(out.omega, om.data(), sizeof(double) * Fb, cudaMemcpyHostToDevice, st));
+    ROM_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * Fb, st));
+    form_reduced_kernel<<<dim3(cdiv(int64_t(k) * ld, 256), Fb), 256, 0, st>>>(KR, DR, MR, fR, k, nrhs, out.omega,
+                                                                             out.G);
+    row_equil_kernel<<<dim3(cdiv(k, 8), Fb), 256, 0, st>>>(out.G, k, nrhs);
+    col_equil_kernel<<<dim3(cdiv(k, 128), Fb), 128, 0, st>>>(out.G, k, nrhs, out.cs);
+    ROM_LAUNCH();
+    partial_lu<double>(out.G, int64_t(k) * ld, ld, Fb, k, ld, k, ipiv, k, status, st);
+    launch_backsub<double>(out.G, int64_t(k) * ld, ld, Fb, k, k, nrhs, st);
+    ROM_LAUNCH();
+    ROM_CUDA(cudaMemcpyAsync(hs.data(), status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
+    ROM_CUDA(cudaStreamSynchronize(st));
+    for (int i = 0; i < Fb; ++i)
+        if (hs[i]) {
+            set_error("singular reduced system");
+            return FSI_ESINGULAR;
+        }
+    return FSI_OK;
+}
+
 }  // namespace fsi
 
 using namespace fsi;
@@ -577,10 +657,10 @@ fsi_status rom_build(const fsi_dims* dims, const void* d_model, const double* sh
     const double2* Fd = reinterpret_cast<const double2*>(F);
     double2* Vd = reinterpret_cast<double2*>(V);
     if (opts->precision == FSI_FP64)
-        return run_rom_build<double>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd,
+        return run_rom_build<double>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd, 0,
                                      k_out, st);
-    return run_rom_build<float>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd, k_out,
-                                st);
+    return run_rom_build<float>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd, 0,
+                                k_out, st);
 }
 
 fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k, const fsi_c64* F, int nrhs,
@@ -625,13 +705,7 @@ fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64*
 
 fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, size_t* bytes) {
     ROM_REQUIRE(k > 0 && nrhs > 0 && nrcv > 0 && batch > 0 && bytes, "bad rom sweep workspace arguments");
-    Carver c(nullptr, 0);
-    c.take<double2>(size_t(batch) * k * (k + nrhs));
-    c.take<int32_t>(size_t(batch) * k);
-    c.take<int32_t>(batch);
-    c.take<double>(size_t(batch) * k);
-    c.take<double>(batch);
-    *bytes = align_up(c.used);
+    *bytes = reduced_solve_ws(k, nrhs, batch);
     return FSI_OK;
 }
 
@@ -641,47 +715,20 @@ fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64*
     ROM_REQUIRE(KR && DR && MR && fR && CR && f_hz && ws && p_out, "NULL argument");
     ROM_REQUIRE(k > 0 && k <= 8192 && nrhs > 0 && nrcv > 0 && nf > 0 && batch > 0, "bad rom sweep sizes");
     const int bt = std::min(batch, nf);
-    Carver c(ws, ws_bytes);
-    double2* G = c.take<double2>(size_t(bt) * k * (k + nrhs));
-    int32_t* ipiv = c.take<int32_t>(size_t(bt) * k);
-    int32_t* status = c.take<int32_t>(bt);
-    double* cs = c.take<double>(size_t(bt) * k);
-    double* omega = c.take<double>(bt);
-    if (!c.fits()) {
-        set_error("rom_sweep workspace too small");
-        return FSI_ENOMEM;
-    }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int ld = k + nrhs;
-    std::vector<double> om(bt);
-    std::vector<int32_t> hs(bt);
-    bool singular = false;
     for (int f0 = 0; f0 < nf; f0 += bt) {
         const int Fb = std::min(bt, nf - f0);
-        for (int i = 0; i < Fb; ++i) om[i] = 2.0 * M_PI * f_hz[f0 + i];
-        ROM_CUDA(cudaMemcpyAsync(omega, om.data(), sizeof(double) * Fb, cudaMemcpyHostToDevice, st));
-        ROM_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * Fb, st));
-        form_reduced_kernel<<<dim3(cdiv(int64_t(k) * ld, 256), Fb), 256, 0, st>>>(
-            reinterpret_cast<const double2*>(KR), reinterpret_cast<const double2*>(DR),
-            reinterpret_cast<const double2*>(MR), reinterpret_cast<const double2*>(fR), k, nrhs, omega, G);
-        row_equil_kernel<<<dim3(cdiv(k, 8), Fb), 256, 0, st>>>(G, k, nrhs);
-        col_equil_kernel<<<dim3(cdiv(k, 128), Fb), 128, 0, st>>>(G, k, nrhs, cs);
-        ROM_LAUNCH();
-        partial_lu<double>(G, int64_t(k) * ld, ld, Fb, k, ld, k, ipiv, k, status, st);
-        launch_backsub<double>(G, int64_t(k) * ld, ld, Fb, k, k, nrhs, st);
-        reduced_receivers_kernel<<<dim3(cdiv(int64_t(nrcv) * nrhs, 128), Fb), 128, 0, st>>>(
-            G, k, nrhs, cs, reinterpret_cast<const double2*>(CR), nrcv,
-            reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs,
-            spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr);
-        ROM_LAUNCH();
-        ROM_CUDA(cudaMemcpyAsync(hs.data(), status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
-        ROM_CUDA(cudaStreamSynchronize(st));
-        for (int i = 0; i < Fb; ++i) singular |= hs[i] != 0;
+        ReducedBatch rb;
+        fsi_status s = reduced_solve_batch(k, reinterpret_cast<const double2*>(KR), reinterpret_cast<const double2*>(DR),
+                                           reinterpret_cast<const double2*>(MR), reinterpret_cast<const double2*>(fR),
+                                           nrhs, f_hz + f0, Fb, ws, ws_bytes, rb, st);
+        if (s != FSI_OK) return s;
+        s = reduced_receivers(rb, reinterpret_cast<const double2*>(CR), nrcv,
+                              reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs,
+                              spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr, st);
+        if (s != FSI_OK) return s;
     }
-    if (singular) {
-        set_error("singular reduced system");
-        return FSI_ESINGULAR;
-    }
+    ROM_CUDA(cudaStreamSynchronize(st));
     return FSI_OK;
 }
 

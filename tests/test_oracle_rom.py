@@ -134,3 +134,19 @@ def test_greedy_picks_worst_candidate_and_improves():
     est = rom.residual_estimate(asm, V1, rom.project(asm, V1, F, rc), F, cand)
     allowed = np.abs(cand - 170.0) > 10.0 * 1.0001
     assert shifts[1] == cand[allowed][int(np.argmax(est[allowed]))]
+
+
+def test_windows_partition_the_band_and_bisect_above_tolerance():
+    w, asm, F, rc = _setup(floor=False)
+    cand = np.arange(40.0, 300.0, 10.0)
+    one = rom.windows(asm, F, rc, cand, q=2, kmax=60, tol=1e3, max_shifts=4, max_windows=8, min_points=3)
+    assert len(one) == 1 and one[0]["lo"] == cand[0] and one[0]["hi"] == cand[-1]
+    wins = rom.windows(asm, F, rc, cand, q=2, kmax=60, tol=1e-6, max_shifts=4, max_windows=4, min_points=3)
+    assert 2 <= len(wins) <= 4
+    # ordered, contiguous cover of the candidates, no point in two windows
+    covered = [c for win in wins for c in cand if win["lo"] <= c <= win["hi"]]
+    assert covered == list(cand)
+    # a window above tolerance could not be split further within the budget
+    for win in wins:
+        npts = sum(1 for c in cand if win["lo"] <= c <= win["hi"])
+        assert win["maxest"] <= 1e-6 or npts < 6 or len(wins) == 4
