@@ -214,3 +214,23 @@ def small_model(nx: int = 5, ny: int = 4, nz: int = 6, Lx: float = 0.6, Ly: floa
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
+
+
+# ----------------------------------------------------------------- learned estimator
+def mlp_init(stream: int = 5) -> np.ndarray:
+    """Seeded initial parameters of the 5-64-64-1 error estimator, flat in the layout
+    [W1 (64x5, row-major), b1, W2 (64x64), b2, W3 (1x64), b3]: Glorot-uniform
+    weights, zero biases (config 5, stream 5)."""
+    rng = _rng(5, stream)
+    parts = []
+    for fan_in, fan_out in ((5, 64), (64, 64), (64, 1)):
+        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        parts.append(rng.uniform(-lim, lim, size=fan_out * fan_in))
+        parts.append(np.zeros(fan_out))
+    return np.concatenate(parts)
+
+
+def mlp_order(n_samples: int, steps: int, batch: int, stream: int = 6) -> np.ndarray:
+    """Seeded mini-batch rows (steps x batch, int32) for training on n_samples rows."""
+    return _rng(5, stream).integers(0, n_samples, size=(steps, batch)).astype(np.int32)
+
