@@ -276,7 +276,24 @@ typedef struct {
     int max_shifts;               /* expansion points at most (initial included)  */
     double tol;                   /* stop when the largest estimate is <= tol      */
     fsi_rom_opts build;           /* factor precision / refinement of the moments */
+    const float* mlp;             /* NULL, or device FSI_MLP_PARAMS of a trained
+                                     estimator: the next point is the allowed
+                                     candidate of largest predicted output error,
+                                     kept only if its residual estimate is > tol
+                                     (else the residual's argmax is taken)       */
 } fsi_greedy_opts;
+
+/* err[f] = |p[f] - p_ref[f]|_F / |p_ref[f]|_F over the nout outputs of each of
+ * nf frequencies (the paper's relative output error; device arrays, p laid out
+ * [nf][nout] as the sweeps write it). */
+fsi_status rom_output_error(const fsi_c64* p_ref, const fsi_c64* p, int nf, int nout, double* err, void* stream);
+
+/* Features of the learned estimator at each candidate (host arrays; X_out
+ * ncand x 5 floats): (f - lo)/(hi - lo); the distances to the three nearest
+ * expansion points over (hi - lo), capped at 1 and 1 where fewer exist;
+ * log10(max(est, 1e-16)) / 4. */
+fsi_status rom_features(const double* cand_hz, int ncand, const double* shifts_hz, int nshift,
+                        const double* est, double lo, double hi, float* X_out);
 
 /* Workspace bytes for rom_greedy (includes one rom_build workspace). */
 fsi_status rom_greedy_workspace(const fsi_dims* dims, int nrhs, const fsi_greedy_opts* opts, size_t* bytes);
@@ -339,6 +356,28 @@ fsi_status rom_windows_sweep(int nwin, const double* lo, const double* hi, const
                              const fsi_c64* fR, const fsi_c64* CR, int nrhs, int nrcv,
                              const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
                              fsi_c64* p_out, double* spl_out, void* stream);
+
+/* Learned ROM error estimator (the paper's Sec. 5 suggests a cheaper error
+ * estimate than full-order checks; this build learns one).  Network 5 -> 64 ->
+ * 64 -> 1, tanh hidden units; parameters flat FP32 [W1 (64x5 row-major), b1,
+ * W2 (64x64), b2, W3 (1x64), b3]; forward/backward with FP16-rounded weight
+ * matrices and FP32 accumulation. */
+#define FSI_MLP_PARAMS 4609
+
+/* Mini-batch Adam (beta 0.9 / 0.999, eps 1e-8) on the mean-squared error of
+ * predictions against T, one persistent launch for all steps.  Device arrays:
+ * params/adam_m/adam_v (FSI_MLP_PARAMS, updated in place; moments start at 0),
+ * X (n x 5 row-major), T (n), order (steps x batch row indices < n), losses
+ * (steps, nullable: mean loss of each step's batch), grad_out (FSI_MLP_PARAMS,
+ * nullable: gradient of the last step).  step0: steps already taken (bias
+ * correction when training resumes).  batch <= 256.  Errors: FSI_EINVAL,
+ * FSI_ECUDA. */
+fsi_status mlp_train(float* params, float* adam_m, float* adam_v, const float* X, const float* T, int n,
+                     const int32_t* order, int steps, int batch, float lr, int step0, float* losses,
+                     float* grad_out, void* stream);
+
+/* y[q] = network(X[q]) for q < n (device arrays). */
+fsi_status mlp_predict(const float* params, const float* X, int n, float* y, void* stream);
 
 const char* fsi_status_str(fsi_status s);
 const char* fsi_last_error(void);

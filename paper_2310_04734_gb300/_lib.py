@@ -47,6 +47,9 @@ class fsi_sweep_stats(C.Structure):
                 ("kernel_flops", C.c_double * 12), ("kernel_launches", C.c_int64 * 12)]
 
 
+MLP_PARAMS = 4609
+
+
 class fsi_rom_opts(C.Structure):
     _fields_ = [("precision", c_int), ("max_refine", c_int), ("tol", C.c_double),
                 ("second_order", c_int)]
@@ -54,7 +57,7 @@ class fsi_rom_opts(C.Structure):
 
 class fsi_greedy_opts(C.Structure):
     _fields_ = [("q", c_int), ("kmax", c_int), ("max_shifts", c_int), ("tol", C.c_double),
-                ("build", fsi_rom_opts)]
+                ("build", fsi_rom_opts), ("mlp", c_void_p)]
 
 
 class fsi_window_opts(C.Structure):
@@ -107,6 +110,11 @@ SIGNATURES = {
     "rom_windows_sweep": (c_int, [c_int, c_double_p, c_double_p, c_int32_p, c_int, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_int, c_int, c_double_p, c_int, c_int, c_void_p, c_size_t,
                                   c_void_p, c_void_p, c_void_p]),
+    "rom_output_error": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
+    "rom_features": (c_int, [c_double_p, c_int, c_double_p, c_int, c_double_p, C.c_double, C.c_double, c_void_p]),
+    "mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
+                          C.c_float, c_int, c_void_p, c_void_p, c_void_p]),
+    "mlp_predict": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
     "fsi_status_str": (C.c_char_p, [c_int]),
     "fsi_last_error": (C.c_char_p, []),
 }

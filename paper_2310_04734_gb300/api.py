@@ -335,7 +335,7 @@ class GreedyResult:
 
 def rom_greedy(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
                init_hz=None, precision="fp32_ir", max_refine=10, refine_tol=1e-10,
-               second_order=-1) -> GreedyResult:
+               second_order=-1, mlp_params=None) -> GreedyResult:
     """Greedy expansion points with the Gram-block residual estimate (C-ABI rom_greedy)."""
     torch = _torch()
     lib = L.load()
@@ -346,6 +346,7 @@ def rom_greedy(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shift
     o = L.fsi_greedy_opts()
     o.q, o.kmax, o.max_shifts, o.tol = int(q), int(kmax), int(max_shifts), float(tol)
     o.build = _rom_opts(precision, max_refine, refine_tol, second_order)
+    o.mlp = _ptr(mlp_params) if mlp_params is not None else None
     need = C.c_size_t()
     L.check(lib.rom_greedy_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_greedy_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
@@ -451,6 +452,76 @@ def rom_windows_sweep(wr: WindowedROM, freqs_hz, batch: int = 256):
                                   _ptr(CR), wr.nrhs, wr.nrcv, f.ctypes.data_as(L.c_double_p), nf, bt, _ptr(ws),
                                   C.c_size_t(need.value), _ptr(p), _ptr(spl), _stream_ptr()), "rom_windows_sweep")
     return p, spl
+
+
+@dataclass
+class MlpState:
+    params: object   # FP32 master parameters (torch, device)
+    m: object        # Adam moments
+    v: object
+    steps: int = 0
+
+
+def mlp_state(init_params) -> MlpState:
+    """Estimator state from flat initial parameters (numpy or torch)."""
+    torch = _torch()
+    p = torch.as_tensor(np.asarray(init_params, dtype=np.float32), device="cuda").contiguous()
+    assert p.numel() == L.MLP_PARAMS
+    return MlpState(params=p, m=torch.zeros_like(p), v=torch.zeros_like(p))
+
+
+def mlp_train(state: MlpState, X, T, order, lr: float = 1e-3, want_grad: bool = False):
+    """Adam steps over the batches order (steps x batch) of rows of X (n x 5), T (n);
+    returns per-step losses (and the last step's gradient)."""
+    torch = _torch()
+    lib = L.load()
+    Xd = torch.as_tensor(np.asarray(X, dtype=np.float32), device="cuda").contiguous()
+    Td = torch.as_tensor(np.asarray(T, dtype=np.float32), device="cuda").contiguous()
+    od = torch.as_tensor(np.asarray(order, dtype=np.int32), device="cuda").contiguous()
+    steps, batch = int(od.shape[0]), int(od.shape[1])
+    losses = torch.empty(steps, dtype=torch.float32, device="cuda")
+    grad = torch.empty(L.MLP_PARAMS, dtype=torch.float32, device="cuda") if want_grad else None
+    L.check(lib.mlp_train(_ptr(state.params), _ptr(state.m), _ptr(state.v), _ptr(Xd), _ptr(Td), int(Xd.shape[0]),
+                          _ptr(od), steps, batch, C.c_float(lr), state.steps, _ptr(losses),
+                          _ptr(grad) if grad is not None else None, _stream_ptr()), "mlp_train")
+    state.steps += steps
+    return (losses, grad) if want_grad else losses
+
+
+def rom_output_error(p_ref, p):
+    """Relative output error per frequency of p against p_ref ([nf][nrcv][nrhs] complex, device)."""
+    torch = _torch()
+    lib = L.load()
+    a = p_ref.contiguous()
+    b = p.contiguous()
+    nf = int(a.shape[0])
+    err = torch.empty(nf, dtype=torch.float64, device=a.device)
+    L.check(lib.rom_output_error(_ptr(a), _ptr(b), nf, int(a[0].numel()), _ptr(err), _stream_ptr()),
+            "rom_output_error")
+    return err
+
+
+def rom_features(cand_hz, shifts_hz, est, lo: float, hi: float) -> np.ndarray:
+    """Estimator features at the candidates (n x 5 float32, host)."""
+    lib = L.load()
+    c = np.ascontiguousarray(np.asarray(cand_hz, dtype=np.float64))
+    sh = np.ascontiguousarray(np.asarray(shifts_hz, dtype=np.float64))
+    e = np.ascontiguousarray(np.asarray(est, dtype=np.float64))
+    X = np.empty((c.size, 5), np.float32)
+    L.check(lib.rom_features(c.ctypes.data_as(L.c_double_p), int(c.size), sh.ctypes.data_as(L.c_double_p),
+                             int(sh.size), e.ctypes.data_as(L.c_double_p), float(lo), float(hi),
+                             X.ctypes.data_as(C.c_void_p)), "rom_features")
+    return X
+
+
+def mlp_predict(params, X):
+    """Network outputs for the rows of X (n x 5)."""
+    torch = _torch()
+    lib = L.load()
+    Xd = torch.as_tensor(np.asarray(X, dtype=np.float32), device="cuda").contiguous()
+    y = torch.empty(int(Xd.shape[0]), dtype=torch.float32, device="cuda")
+    L.check(lib.mlp_predict(_ptr(params), _ptr(Xd), int(Xd.shape[0]), _ptr(y), _stream_ptr()), "mlp_predict")
+    return y
 
 
 def load_matrix_dofs(spec, loads, n_rhs):

@@ -56,6 +56,22 @@ constexpr int kCandBatch = 128;  // candidate frequencies per reduced-solve batc
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
+// Estimator features of candidate i: position in the band, distances to the three nearest
+// expansion points (band-relative, 1 when missing), log10 of the residual estimate / 4.
+void features(const double* cand, int ncand, const double* shifts, int nshift, const double* est, double lo,
+              double hi, float* X) {
+    const double span = hi > lo ? hi - lo : 1.0;
+    std::vector<double> d(nshift);
+    for (int i = 0; i < ncand; ++i) {
+        for (int j = 0; j < nshift; ++j) d[j] = std::fabs(cand[i] - shifts[j]) / span;
+        std::sort(d.begin(), d.end());
+        float* x = X + int64_t(i) * 5;
+        x[0] = float((cand[i] - lo) / span);
+        for (int j = 0; j < 3; ++j) x[1 + j] = float(j < nshift ? std::min(d[j], 1.0) : 1.0);
+        x[4] = float(std::log10(std::max(est[i], 1e-16)) / 4.0);
+    }
+}
+
 // weight of row i: 1 (sel 0); on the fluid rows 1/(rho |K_ii|) (sel 1); on the shell rows 1/|K_ii| (sel 2)
 __device__ __forceinline__ double row_weight(const DevModel& m, int64_t i, int sel) {
     if (sel == 0) return 1.0;
@@ -236,6 +252,7 @@ struct GreedyWS {
     size_t build_bytes = 0;
     double2 *Y, *P, *Pf, *Gf, *Gs, *Hf, *Hs, *part;
     double *fnf, *fns, *num, *den;
+    float *xf = nullptr, *yf = nullptr;   // estimator features / predictions of one candidate batch
     void* rws = nullptr;
     size_t rws_bytes = 0;
     int64_t ldp = 0, ldg = 0;
@@ -264,6 +281,8 @@ struct GreedyWS {
         den = c.take<double>(size_t(kCandBatch) * nrhs);
         rws_bytes = reduced_solve_ws(K, nrhs, kCandBatch);
         rws = c.take<char>(rws_bytes);
+        xf = c.take<float>(size_t(kCandBatch) * 5);
+        yf = c.take<float>(kCandBatch);
     }
 };
 
@@ -380,19 +399,39 @@ fsi_status run_greedy(const fsi_dims& d, const void* d_model, const double2* F, 
         if (hist_out && nhist < o.max_shifts) hist_out[nhist] = emax;
         ++nhist;
         if (emax <= o.tol || int(shifts.size()) >= o.max_shifts || k >= o.kmax) break;
-        std::vector<int> order(ncand);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return est[a] > est[b]; });
-        double nxt = -1.0;
-        for (int i : order) {
-            bool ok = true;
-            for (double sh : shifts) ok = ok && std::fabs(cand[i] - sh) > step * 1.0001;
-            if (ok) {
-                nxt = cand[i];
-                break;
+        auto allowed = [&](int i) {
+            for (double sh : shifts)
+                if (!(std::fabs(cand[i] - sh) > step * 1.0001)) return false;
+            return true;
+        };
+        auto pick = [&](const std::vector<double>& score) {
+            std::vector<int> order(ncand);
+            std::iota(order.begin(), order.end(), 0);
+            std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return score[a] > score[b]; });
+            for (int i : order)
+                if (allowed(i)) return i;
+            return -1;
+        };
+        int inext = -1;
+        if (o.mlp) {
+            // learned estimate of the output error; the residual estimate confirms the choice
+            std::vector<float> hx(size_t(ncand) * 5), hy(ncand);
+            features(cand, ncand, shifts.data(), int(shifts.size()), est.data(), cand[0], cand[ncand - 1], hx.data());
+            for (int f0 = 0; f0 < ncand; f0 += kCandBatch) {
+                const int Fb = std::min(kCandBatch, ncand - f0);
+                GR_CUDA(cudaMemcpyAsync(w.xf, hx.data() + size_t(f0) * 5, sizeof(float) * Fb * 5,
+                                        cudaMemcpyHostToDevice, st));
+                s = mlp_predict(o.mlp, w.xf, Fb, w.yf, st);
+                if (s != FSI_OK) return s;
+                GR_CUDA(cudaMemcpyAsync(hy.data() + f0, w.yf, sizeof(float) * Fb, cudaMemcpyDeviceToHost, st));
+                GR_CUDA(cudaStreamSynchronize(st));
             }
+            const int i = pick(std::vector<double>(hy.begin(), hy.end()));
+            if (i >= 0 && est[i] > o.tol) inext = i;
         }
-        if (nxt < 0.0) break;
+        if (inext < 0) inext = pick(est);
+        if (inext < 0) break;
+        double nxt = cand[inext];
         shifts.push_back(nxt);
         s = rom_build_append<R>(d, d_model, &nxt, 1, o.q, F, nrhs, o.kmax, o.build, w.build, w.build_bytes, V, k, &k1,
                                 st);
@@ -411,6 +450,37 @@ fsi_status run_greedy(const fsi_dims& d, const void* d_model, const double2* F, 
     *nshift_out = int(shifts.size());
     if (est_out) std::copy(est.begin(), est.end(), est_out);
     return FSI_OK;
+}
+
+// err[f] = |p_ref[f] - p[f]|_F / |p_ref[f]|_F over the m = nrcv * nrhs outputs of frequency f
+__global__ void output_error_kernel(const double2* pref, const double2* p, int nf, int m, double* err) {
+    const int f = blockIdx.x;
+    if (f >= nf) return;
+    double a = 0.0, b = 0.0;
+    for (int q = threadIdx.x; q < m; q += blockDim.x) {
+        const double2 r = pref[int64_t(f) * m + q], x = p[int64_t(f) * m + q];
+        const double dx = x.x - r.x, dy = x.y - r.y;
+        a += dx * dx + dy * dy;
+        b += r.x * r.x + r.y * r.y;
+    }
+    __shared__ double sa[32], sb[32];
+    for (int off = 16; off > 0; off >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, off);
+        b += __shfl_down_sync(0xffffffffu, b, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sa[threadIdx.x >> 5] = a;
+        sb[threadIdx.x >> 5] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tb = 0.0;
+        for (int w = 0; w < int(blockDim.x >> 5); ++w) {
+            ta += sa[w];
+            tb += sb[w];
+        }
+        err[f] = tb > 0.0 ? sqrt(ta / tb) : 0.0;
+    }
 }
 
 struct WindowResult {
@@ -485,6 +555,27 @@ size_t greedy_ws_bytes(const fsi_dims& d, int nrhs, const fsi_greedy_opts& o) {
 using namespace fsi;
 
 extern "C" {
+
+fsi_status rom_output_error(const fsi_c64* p_ref, const fsi_c64* p, int nf, int nout, double* err, void* stream) {
+    if (!(p_ref && p && err && nf > 0 && nout > 0)) {
+        set_error("rom_output_error: bad arguments");
+        return FSI_EINVAL;
+    }
+    output_error_kernel<<<nf, 128, 0, static_cast<cudaStream_t>(stream)>>>(
+        reinterpret_cast<const double2*>(p_ref), reinterpret_cast<const double2*>(p), nf, nout, err);
+    GR_CUDA(cudaGetLastError());
+    return FSI_OK;
+}
+
+fsi_status rom_features(const double* cand_hz, int ncand, const double* shifts_hz, int nshift, const double* est,
+                        double lo, double hi, float* X_out) {
+    if (!(cand_hz && est && X_out && ncand > 0 && nshift >= 0 && (nshift == 0 || shifts_hz))) {
+        set_error("rom_features: bad arguments");
+        return FSI_EINVAL;
+    }
+    features(cand_hz, ncand, shifts_hz, nshift, est, lo, hi, X_out);
+    return FSI_OK;
+}
 
 fsi_status rom_greedy_workspace(const fsi_dims* dims, int nrhs, const fsi_greedy_opts* o, size_t* bytes) {
     if (!(dims && o && bytes && nrhs > 0 && nrhs <= 8 && o->q > 0 && o->kmax > 0)) {

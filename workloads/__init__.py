@@ -201,6 +201,31 @@ def config5_variants(count: int = 64) -> List[Workload]:
     return out
 
 
+def config5_reduced_variants(count: int = 64) -> List[Workload]:
+    """Config 5's design study at a scale one GPU runs in minutes: the same variant
+    recipe (seeded nz, two cross-sections, shell thickness U[1.5, 3] mm, floor
+    impedance rho*c*(a - 1i), a U[1, 4]; one load) on coarse meshes -- nz U{10..20}
+    slabs of 6 x 6 (0.6 x 0.6 m) or 8 x 8 (0.8 x 0.8 m) nodes, axial spacing 0.1 m --
+    8 receivers, 96 frequencies on a 4 Hz grid over 20-400 Hz."""
+    rng = _rng(5, 7)
+    out = []
+    freqs = 20.0 + 4.0 * np.arange(96, dtype=np.float64)
+    for v in range(count):
+        nz = int(rng.integers(10, 21))
+        big = bool(rng.integers(0, 2))
+        t = float(rng.uniform(1.5e-3, 3e-3))
+        a = float(rng.uniform(1.0, 4.0))
+        nxy = 8 if big else 6
+        L = 0.8 if big else 0.6
+        m = ModelSpec(Lx=L, Ly=L, Lz=(nz - 1) * 0.1, nx=nxy, ny=nxy, nz=nz, t=t,
+                      eta=(0.01,) * (nz - 1), Z_floor=AIR_RHO * AIR_C * (a - 1.0j))
+        cid = 2000 + v
+        out.append(Workload(name=f"cfg5r_variant{v:02d}", config_id=cid, model=m,
+                            loads=_shell_loads(cid, nz, m.n_ring, 1), n_rhs=1,
+                            receivers=_receivers(cid, nxy, nxy, nz, 8), freqs_hz=freqs))
+    return out
+
+
 def small_model(nx: int = 5, ny: int = 4, nz: int = 6, Lx: float = 0.6, Ly: float = 0.5,
                 Lz: float = 1.0, floor: bool = True, eta: float = 0.02, t: float = SHELL_T,
                 cfg_id: int = 99, n_loads: int = 2, n_rcv: int = 4) -> Workload:
