@@ -357,6 +357,34 @@ fsi_status rom_windows_sweep(int nwin, const double* lo, const double* hi, const
                              const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
                              fsi_c64* p_out, double* spl_out, void* stream);
 
+/* One reduced model of a multi-model reduced sweep (all pointers device; the
+ * matrices as rom_project writes them: KR/DR/MR k x k, fR k x nrhs, CR nrcv x k,
+ * column-major).  k <= 128, nrhs <= 4. */
+typedef struct {
+    int k, nrhs, nrcv, nf;
+    const fsi_c64* KR;
+    const fsi_c64* DR;
+    const fsi_c64* MR;
+    const fsi_c64* fR;
+    const fsi_c64* CR;
+    const double* f_hz;           /* nf frequencies                                  */
+    fsi_c64* p_out;               /* nf x nrcv x nrhs                                */
+    double* spl_out;              /* same shape, nullable                            */
+} fsi_rom_item;
+
+/* Reduced sweeps (Eq. 11) of nvar models of uneven size in one persistent
+ * launch: CTAs take (model, frequency) items, numbered model by model (offsets:
+ * device prefix sums of the models' nf, nvar + 1 entries; total = offsets[nvar])
+ * from a counter (device int, reset by the call); each item is equilibrated,
+ * factored by LU with partial pivoting in FP32 and refined against the FP64
+ * residual until the correction is at rounding level (at most 8 steps), then
+ * projected to the receivers.  items: device array.
+ * Enqueues only a memset and one kernel on the stream (capturable into a CUDA
+ * graph); status (device, total, nullable): 0, 1 for a zero or non-finite
+ * pivot, 2 for a descriptor out of range.  Errors: FSI_EINVAL, FSI_ECUDA. */
+fsi_status rom_multi_sweep(const fsi_rom_item* items, int nvar, const int32_t* offsets, int total,
+                           int* counter, int32_t* status, void* stream);
+
 /* Learned ROM error estimator (the paper's Sec. 5 suggests a cheaper error
  * estimate than full-order checks; this build learns one).  Network 5 -> 64 ->
  * 64 -> 1, tanh hidden units; parameters flat FP32 [W1 (64x5 row-major), b1,

@@ -64,6 +64,12 @@ class fsi_window_opts(C.Structure):
     _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int)]
 
 
+class fsi_rom_item(C.Structure):
+    _fields_ = [("k", c_int), ("nrhs", c_int), ("nrcv", c_int), ("nf", c_int), ("KR", c_void_p), ("DR", c_void_p),
+                ("MR", c_void_p), ("fR", c_void_p), ("CR", c_void_p), ("f_hz", c_void_p), ("p_out", c_void_p),
+                ("spl_out", c_void_p)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "fsi_model_dims": (c_int, [C.POINTER(fsi_model_desc), C.POINTER(fsi_dims)]),
@@ -112,6 +118,7 @@ SIGNATURES = {
                                   c_void_p, c_void_p, c_void_p]),
     "rom_output_error": (c_int, [c_void_p, c_void_p, c_int, c_int, c_void_p, c_void_p]),
     "rom_features": (c_int, [c_double_p, c_int, c_double_p, c_int, c_double_p, C.c_double, C.c_double, c_void_p]),
+    "rom_multi_sweep": (c_int, [c_void_p, c_int, c_void_p, c_int, c_void_p, c_void_p, c_void_p]),
     "mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                           C.c_float, c_int, c_void_p, c_void_p, c_void_p]),
     "mlp_predict": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),

@@ -524,6 +524,52 @@ def mlp_predict(params, X):
     return y
 
 
+class MultiSweep:
+    """Reduced sweeps of several ROMs in one persistent launch (C-ABI rom_multi_sweep).
+
+    Buffers (descriptors, prefix sums, queue counter, outputs) are made once; launch()
+    only enqueues device work on the current stream, so it can be captured into a
+    CUDA graph and replayed.  Models are queued in order of decreasing k."""
+
+    def __init__(self, roms: Sequence[DeviceROM], freqs: Sequence[Sequence[float]]):
+        torch = _torch()
+        assert len(roms) == len(freqs) and len(roms) > 0
+        cm = lambda X: X.t().contiguous()
+        self.order = sorted(range(len(roms)), key=lambda i: -roms[i].k)
+        self._keep = []
+        self.p = [None] * len(roms)
+        self.spl = [None] * len(roms)
+        items = (L.fsi_rom_item * len(roms))()
+        off = [0]
+        for slot, i in enumerate(self.order):
+            r = roms[i]
+            if r.k > 128 or r.fR.shape[1] > 4:
+                raise ValueError("rom_multi_sweep handles k <= 128 and at most 4 load columns")
+            f = torch.as_tensor(np.asarray(freqs[i], dtype=np.float64), device="cuda")
+            nf, nrcv, nrhs = int(f.numel()), int(r.CR.shape[0]), int(r.fR.shape[1])
+            bufs = (cm(r.KR), cm(r.DR), cm(r.MR), cm(r.fR), cm(r.CR), f)
+            self.p[i] = torch.empty((nf, nrcv, nrhs), dtype=torch.complex128, device="cuda")
+            self.spl[i] = torch.empty((nf, nrcv, nrhs), dtype=torch.float64, device="cuda")
+            self._keep.append(bufs)
+            it = items[slot]
+            it.k, it.nrhs, it.nrcv, it.nf = r.k, nrhs, nrcv, nf
+            it.KR, it.DR, it.MR, it.fR, it.CR, it.f_hz = (b.data_ptr() for b in bufs)
+            it.p_out, it.spl_out = self.p[i].data_ptr(), self.spl[i].data_ptr()
+            off.append(off[-1] + nf)
+        raw = bytes(items)
+        self.items = torch.tensor(list(raw), dtype=torch.uint8, device="cuda")
+        self.offsets = torch.tensor(off, dtype=torch.int32, device="cuda")
+        self.total = off[-1]
+        self.counter = torch.zeros(1, dtype=torch.int32, device="cuda")
+        self.status = torch.zeros(self.total, dtype=torch.int32, device="cuda")
+        self.nvar = len(roms)
+
+    def launch(self):
+        lib = L.load()
+        L.check(lib.rom_multi_sweep(_ptr(self.items), self.nvar, _ptr(self.offsets), self.total, _ptr(self.counter),
+                                    _ptr(self.status), _stream_ptr()), "rom_multi_sweep")
+
+
 def load_matrix_dofs(spec, loads, n_rhs):
     """Load columns as (DoF index, column, value) triplets for the slab-major numbering."""
     npl = spec.nx * spec.ny

@@ -87,3 +87,24 @@ def linear_baseline(train: List[VariantData]):
     A = np.stack([x, np.ones_like(x)], axis=1)
     coef, *_ = np.linalg.lstsq(A, t, rcond=None)
     return coef
+
+
+def variant_rom(w, q: int, kmax: int, max_shifts: int, tol: float, mlp_params=None):
+    """Greedy ROM of one variant over its frequency grid (residual- or estimator-driven)."""
+    model, F, rcv = _setup(w)
+    cand = np.asarray(w.freqs_hz, dtype=np.float64)
+    g = api.rom_greedy(model, F, rcv, cand, q=q, kmax=kmax, max_shifts=max_shifts, tol=tol, mlp_params=mlp_params)
+    return g, (model, F, rcv)
+
+
+def check_variant(w, handles, p_rom, check_idx):
+    """Full-order solutions at the check frequencies and the ROM's SPL error there (dB);
+    frequencies above 0.1 dB are the ones to re-solve at full order."""
+    model, F, rcv = handles
+    f = np.asarray(w.freqs_hz, dtype=np.float64)[check_idx]
+    r = api.frf_sweep_full(model, f, F, rcv, precision="fp32_ir", batch=len(f), max_refine=60, tol=1e-10,
+                           allow_noconv=True)
+    pf = r.p.cpu().numpy()
+    pr = p_rom[check_idx].cpu().numpy()
+    db = np.abs(20.0 * np.log10(np.abs(pr) / np.abs(pf))).max(axis=(1, 2))
+    return db, pf

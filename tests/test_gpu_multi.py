@@ -1,0 +1,67 @@
+"""Persistent multi-model reduced sweep (uneven reduced orders in one launch) against
+the per-model FP64 reduced sweep, and its replay from a captured CUDA graph."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import need_cuda, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def _roms():
+    from paper_2310_04734_gb300 import api
+    import torch
+    roms, freqs = [], []
+    cases = [(2, True, (5, 4, 6), 31), (3, False, (4, 5, 7), 32), (4, True, (5, 5, 8), 33), (12, True, (6, 5, 9), 34)]
+    for q, floor, (nx, ny, nz), cid in cases:
+        w = W.small_model(nx=nx, ny=ny, nz=nz, floor=floor, n_loads=2, n_rcv=4, cfg_id=cid)
+        model = api.fsi_assemble(w.model)
+        F = api.dense_loads(w.model, w.loads, w.n_rhs)
+        rcv = torch.tensor(api.receiver_dofs(w.model, w.receivers), device="cuda")
+        V = api.rom_build(model, [60.0, 150.0, 250.0], q, F, kmax=128, precision="fp64", max_refine=4, tol=1e-13)
+        roms.append(api.rom_project(model, V, F, rcv))
+        freqs.append(np.linspace(35.0, 290.0, 11 + 3 * q))
+    return roms, freqs
+
+
+def test_multi_sweep_matches_per_model_sweeps():
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    roms, freqs = _roms()
+    assert len({r.k for r in roms}) == len(roms) and max(r.k for r in roms) > 64
+    ms = api.MultiSweep(roms, freqs)
+    ms.launch()
+    torch.cuda.synchronize()
+    assert int(ms.status.sum().item()) == 0
+    for rm, f, p, spl in zip(roms, freqs, ms.p, ms.spl):
+        pref, splref = api.rom_sweep(rm, f, batch=16)
+        assert rel(p.cpu().numpy(), pref.cpu().numpy()) <= 1e-6
+        assert np.abs(spl.cpu().numpy() - splref.cpu().numpy()).max() <= 1e-4
+
+
+def test_multi_sweep_replays_from_a_cuda_graph():
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    roms, freqs = _roms()
+    ms = api.MultiSweep(roms, freqs)
+    ms.launch()
+    torch.cuda.synchronize()
+    ref = [p.clone() for p in ms.p]
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        ms.launch()   # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    for p in ms.p:
+        p.zero_()
+    with torch.cuda.graph(g):
+        ms.launch()
+    for p in ms.p:
+        p.zero_()
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(ref, ms.p))
