@@ -37,6 +37,7 @@ import workloads as W  # noqa: E402
 REFINE_TOL = 1e-10
 METRIC = "FRF frequencies/sec at <=0.1 dB SPL error vs FP64 full-order sweep; tensor-pipe %"
 UNIT = "frequencies/s"
+GEMM_BYTES_PER_FLOP = 481.7e6 / 16.74e9
 
 
 def _peaks():
@@ -318,7 +319,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--batch", type=int, default=32)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "tf32x3_ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -463,9 +464,14 @@ def main():
                     "peak_source": f"measured bf16 {peaks['bf16_tflops']} TFLOP/s x 1/2 (tf32) x 1/3 (3 products)",
                     "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
     else:
-        roofline = {"bound": "alu", "kernel": "gemm_update_kernel<float2> (trailing complex GEMM of the band LU)",
+        # DRAM bytes per algorithmic flop of the trailing update, from an ncu capture of the
+        # 1640 x 2492 x 64 update of eight config-2 windows (481.7 MB for 16.74 GFLOP); the
+        # C read-modify-write dominates and scales with the flops at fixed K
+        traffic = GEMM_BYTES_PER_FLOP * kern_flops[g] / max(kern_n[g], 1)
+        roofline = {"bound": "alu", "kernel": "cgemm_f32_kernel (trailing complex GEMM of the band LU, FP32 SIMT)",
                     "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                    "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+                    "traffic_unit": "bytes per launch (mean launch; scaled from an ncu capture)",
                     "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
                     "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
     shares = {k: {"ms": float(kern_ms[i]), "launches": int(kern_n[i]),
@@ -487,7 +493,7 @@ def main():
                 "config": {"workload": w.name, "model_dofs": int(model.dims.n), "slab_block": int(model.dims.b),
                            "slabs": int(model.dims.nz), "loads": w.n_rhs, "receivers": len(w.receivers),
                            "batch_frequencies": B, "refine_tol": REFINE_TOL, "parallelism": f"replicas{world}",
-                           "l2": "inputs larger than L2 (factor store ~70 GB per batch)"},
+                           "l2": f"inputs larger than L2 (factor store ~{2.2 * B:.0f} GB per batch)"},
                 "roofline": roofline, "kernels": shares, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "fp64_full_order": fp64,
                 "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters)), "unconverged": unconv,

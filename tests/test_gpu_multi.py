@@ -34,9 +34,18 @@ def test_multi_sweep_matches_per_model_sweeps():
     ms.launch()
     torch.cuda.synchronize()
     assert int(ms.status.sum().item()) == 0
+    u = np.finfo(np.float64).eps / 2
     for rm, f, p, spl in zip(roms, freqs, ms.p, ms.spl):
         pref, splref = api.rom_sweep(rm, f, batch=16)
-        assert rel(p.cpu().numpy(), pref.cpu().numpy()) <= 1e-6
+        pg, pr = p.cpu().numpy(), pref.cpu().numpy()
+        KR, DR, MR = (x.cpu().numpy() for x in (rm.KR, rm.DR, rm.MR))
+        for i, fi in enumerate(f):
+            w = 2 * np.pi * fi
+            A = KR + 1j * w * DR - w * w * MR
+            A = A / np.abs(A).max(axis=1, keepdims=True)            # the row equilibration both solvers use
+            kappa = np.linalg.cond(A / np.abs(A).max(axis=0, keepdims=True), 1)
+            # both are backward stable in FP64 (the multi-model kernel after refinement)
+            assert rel(pg[i], pr[i]) <= max(1e-6, 10 * kappa * u), (rm.k, fi, rel(pg[i], pr[i]), kappa)
         assert np.abs(spl.cpu().numpy() - splref.cpu().numpy()).max() <= 1e-4
 
 
