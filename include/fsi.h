@@ -381,7 +381,10 @@ typedef struct {
  * projected to the receivers.  items: device array.
  * Enqueues only a memset and one kernel on the stream (capturable into a CUDA
  * graph); status (device, total, nullable): 0, 1 for a zero or non-finite
- * pivot, 2 for a descriptor out of range.  Errors: FSI_EINVAL, FSI_ECUDA. */
+ * pivot, 2 for a descriptor out of range, 3 when the refinement did not reach
+ * a correction below 1e-12 of the solution (reduced system too ill-conditioned
+ * for the FP32 factor: re-solve the item with rom_sweep).  Errors: FSI_EINVAL,
+ * FSI_ECUDA. */
 fsi_status rom_multi_sweep(const fsi_rom_item* items, int nvar, const int32_t* offsets, int total,
                            int* counter, int32_t* status, void* stream);
 

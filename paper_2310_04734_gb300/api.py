@@ -569,6 +569,24 @@ class MultiSweep:
         L.check(lib.rom_multi_sweep(_ptr(self.items), self.nvar, _ptr(self.offsets), self.total, _ptr(self.counter),
                                     _ptr(self.status), _stream_ptr()), "rom_multi_sweep")
 
+    def fixup(self, roms, freqs) -> int:
+        """Re-solve with the FP64 reduced sweep the items whose refinement did not converge
+        (status 3); returns their number.  Items with a singular pivot stay flagged."""
+        st = self.status.cpu().numpy()
+        off = self.offsets.cpu().numpy()
+        fixed = 0
+        for slot, i in enumerate(self.order):
+            bad = np.nonzero(st[off[slot]:off[slot + 1]] == 3)[0]
+            if bad.size == 0:
+                continue
+            f = np.asarray(freqs[i], dtype=np.float64)[bad]
+            p, spl = rom_sweep(roms[i], f, batch=max(1, min(64, bad.size)))
+            idx = _torch().as_tensor(bad, device="cuda")
+            self.p[i][idx] = p
+            self.spl[i][idx] = spl
+            fixed += int(bad.size)
+        return fixed
+
 
 def load_matrix_dofs(spec, loads, n_rhs):
     """Load columns as (DoF index, column, value) triplets for the slab-major numbering."""

@@ -63,6 +63,8 @@ DevModel dev_model(const fsi_dims& d, const void* blob) {
     m.M = reinterpret_cast<const double*>(b + L.M);
     m.D = reinterpret_cast<const double2*>(b + L.D);
     m.kdiag = reinterpret_cast<const double*>(b + L.kdiag);
+    m.cbase = reinterpret_cast<const double*>(b + L.cbase);
+    m.rbase = reinterpret_cast<const double*>(b + L.rbase);
     m.n = d.n;
     m.b = d.b;
     m.nz = d.nz;
@@ -397,6 +399,17 @@ fsi_status fsi_assemble(const fsi_model_desc* desc, void* d_model, size_t model_
     FSI_CUDA(cudaMemcpyAsync(b + L.D, hm.D.data(), sizeof(fsi_c64) * hm.D.size(), cudaMemcpyHostToDevice, st));
     FSI_CUDA(cudaMemcpyAsync(b + L.kdiag, hm.kdiag.data(), sizeof(double) * hm.kdiag.size(), cudaMemcpyHostToDevice,
                              st));
+    // frequency-independent factors of the equilibration: column scale = cbase (shell) or
+    // |cbase| w (fluid, stored negative), row scale = rbase (shell) or |rbase| / w (fluid)
+    std::vector<double> cb(hm.kdiag.size()), rb(hm.kdiag.size());
+    for (size_t g = 0; g < cb.size(); ++g) {
+        const double kd = hm.kdiag[g];
+        const bool fluid = int64_t(g % size_t(hm.dims.b)) < hm.dims.n_press_slab;
+        cb[g] = fluid ? -std::sqrt(hm.dims.rho / kd) : 1.0 / std::sqrt(kd);
+        rb[g] = fluid ? -(1.0 / std::sqrt(hm.dims.rho * kd)) : 1.0 / std::sqrt(kd);
+    }
+    FSI_CUDA(cudaMemcpyAsync(b + L.cbase, cb.data(), sizeof(double) * cb.size(), cudaMemcpyHostToDevice, st));
+    FSI_CUDA(cudaMemcpyAsync(b + L.rbase, rb.data(), sizeof(double) * rb.size(), cudaMemcpyHostToDevice, st));
     FSI_CUDA(cudaStreamSynchronize(st));
     return FSI_OK;
 }

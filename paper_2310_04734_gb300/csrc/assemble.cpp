@@ -157,6 +157,8 @@ ModelLayout model_layout(const fsi_dims& d) {
     L.M = put(sizeof(double) * d.nnz);
     L.D = put(sizeof(fsi_c64) * d.nnz);
     L.kdiag = put(sizeof(double) * d.n);
+    L.cbase = put(sizeof(double) * d.n);
+    L.rbase = put(sizeof(double) * d.n);
     L.total = align_up(off);
     return L;
 }

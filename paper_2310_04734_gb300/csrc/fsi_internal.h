@@ -18,7 +18,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
 // Byte offsets of the arrays inside the device model buffer.
 struct ModelLayout {
-    size_t rowptr, col, K, M, D, kdiag, total;
+    size_t rowptr, col, K, M, D, kdiag, cbase, rbase, total;
 };
 ModelLayout model_layout(const fsi_dims& d);
 

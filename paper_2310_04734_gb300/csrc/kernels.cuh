@@ -15,6 +15,8 @@ struct DevModel {
     const double* M;
     const double2* D;
     const double* kdiag;
+    const double* cbase;   // scale factors without their w dependence (negative on fluid rows)
+    const double* rbase;
     int64_t n;
     int b, nz, npl;
     double rho;
@@ -78,12 +80,12 @@ __device__ __forceinline__ T2 cinv(T2 a) {
 // symmetric Jacobi scaling by |K_ii|^-1/2 is applied.
 __device__ __forceinline__ bool is_fluid(const DevModel& m, int64_t g) { return (g % m.b) < m.npl; }
 __device__ __forceinline__ double row_scale(const DevModel& m, int64_t g, double w) {
-    const double kd = m.kdiag[g];
-    return is_fluid(m, g) ? 1.0 / (w * sqrt(m.rho * kd)) : 1.0 / sqrt(kd);
+    const double r = m.rbase[g];   // fluid: 1/(w sqrt(rho |K_ii|)), shell: 1/sqrt(|K_ii|)
+    return r < 0.0 ? -r / w : r;
 }
 __device__ __forceinline__ double col_scale(const DevModel& m, int64_t g, double w) {
-    const double kd = m.kdiag[g];
-    return is_fluid(m, g) ? w * sqrt(m.rho / kd) : 1.0 / sqrt(kd);
+    const double c = m.cbase[g];   // fluid: w sqrt(rho / |K_ii|), shell: 1/sqrt(|K_ii|)
+    return c < 0.0 ? -c * w : c;
 }
 // A(w)_e = K_e + i w D_e - w^2 M_e
 __device__ __forceinline__ double2 a_entry(const DevModel& m, int64_t e, double w) {

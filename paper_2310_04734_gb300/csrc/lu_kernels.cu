@@ -114,16 +114,17 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG,
     const int f = blockIdx.x;
     T2* A = G + f * sG;
     const int mr = m - j0;
+    const int ms = mr | 1;   // odd column stride: the 8/16-byte row-wise stores hit distinct banks
     for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
         const int i = idx / nbw, t = idx - i * nbw;
-        P[t * mr + i] = A[int64_t(j0 + i) * ld + j0 + t];
+        P[t * ms + i] = A[int64_t(j0 + i) * ld + j0 + t];
     }
     __syncthreads();
     for (int t = 0; t < nbw; ++t) {
         R best = R(-1);
         int bi = 0x7fffffff;
         for (int i = t + threadIdx.x; i < mr; i += blockDim.x) {
-            const T2 v = P[t * mr + i];
+            const T2 v = P[t * ms + i];
             const R a = v.x * v.x + v.y * v.y;
             if (a > best || (a == best && i < bi)) {
                 best = a;
@@ -143,23 +144,23 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG,
         if (threadIdx.x == 0) ipiv[f * sP + j0 + t] = j0 + bi;
         if (bi != t) {
             for (int u = threadIdx.x; u < nbw; u += blockDim.x) {
-                const T2 x = P[u * mr + t];
-                P[u * mr + t] = P[u * mr + bi];
-                P[u * mr + bi] = x;
+                const T2 x = P[u * ms + t];
+                P[u * ms + t] = P[u * ms + bi];
+                P[u * ms + bi] = x;
             }
         }
         __syncthreads();
-        const T2 inv = cinv(P[t * mr + t]);
+        const T2 inv = cinv(P[t * ms + t]);
         for (int i = t + 1 + threadIdx.x; i < mr; i += blockDim.x) {
-            const T2 l = cmul(P[t * mr + i], inv);
-            P[t * mr + i] = l;
-            for (int u = t + 1; u < nbw; ++u) cfms(P[u * mr + i], l, P[u * mr + t]);
+            const T2 l = cmul(P[t * ms + i], inv);
+            P[t * ms + i] = l;
+            for (int u = t + 1; u < nbw; ++u) cfms(P[u * ms + i], l, P[u * ms + t]);
         }
         __syncthreads();
     }
     for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
         const int i = idx / nbw, t = idx - i * nbw;
-        A[int64_t(j0 + i) * ld + j0 + t] = P[t * mr + i];
+        A[int64_t(j0 + i) * ld + j0 + t] = P[t * ms + i];
     }
 }
 
@@ -400,7 +401,7 @@ template <typename R>
 int panel_width(int m) {
     const size_t el = sizeof(typename Cplx<R>::T);
     for (int w = 32; w >= 2; w >>= 1)
-        if (size_t(m) * w * el + 64 * (sizeof(double) + sizeof(int)) <= kMaxPanelSmem) return w;
+        if (size_t(m + 1) * w * el + 64 * (sizeof(double) + sizeof(int)) <= kMaxPanelSmem) return w;
     return 1;
 }
 
@@ -413,7 +414,7 @@ template <typename R>
 void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int j0, int nbw, int32_t* ipiv,
                   int64_t sP, int32_t* status, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
-    const size_t smem = 64 * (sizeof(double) + sizeof(int)) + size_t(m - j0) * nbw * sizeof(T2);
+    const size_t smem = 64 * (sizeof(double) + sizeof(int)) + size_t((m - j0) | 1) * nbw * sizeof(T2);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(panel_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem + 2048));

@@ -12,7 +12,9 @@
 //   at FP64 rounding level (at most 8); p = C_R x, SPL.
 // The launch only enqueues a memset of the counter and the kernel (no host
 // synchronisation, no allocation), so it can be captured into a CUDA graph.
-// A status word per item records a zero or non-finite pivot.
+// A status word per item records a zero or non-finite pivot, or a refinement that
+// did not converge (a reduced system too ill-conditioned for its FP32 factor; the
+// caller re-solves those items in FP64).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -228,6 +230,7 @@ __global__ void __launch_bounds__(kMT) rom_multi_kernel(const fsi_rom_item* item
             S.r[i * kRMax + c] = fR[int64_t(c) * k + i];
         }
         __syncthreads();
+        bool conv = false;
         for (int pass = 0; pass <= kRefine; ++pass) {
             for (int q = tid; q < k * nr; q += blockDim.x) {
                 const int i = q / nr, c = q - i * nr;
@@ -262,6 +265,7 @@ __global__ void __launch_bounds__(kMT) rom_multi_kernel(const fsi_rom_item* item
                 xall = fmaxf(xall, __int_as_float(S.ri[q]));
             }
             __syncthreads();
+            conv = dall <= 1e-12f * xall;
             if (pass == kRefine || dall <= 1e-15f * xall) break;
             for (int q = tid; q < k * nr; q += blockDim.x) {
                 const int i = q / nr, c = q - i * nr;
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kMT) rom_multi_kernel(const fsi_rom_item* item
                 it.spl_out[int64_t(fi) * it.nrcv * nr + q] =
                     20.0 * log10(sqrt(acc.x * acc.x + acc.y * acc.y) / (sqrt(2.0) * 2e-5));
         }
-        if (tid == 0 && status) status[g] = S.bad;
+        if (tid == 0 && status) status[g] = S.bad ? 1 : (conv ? 0 : 3);
         __syncthreads();
     }
 }

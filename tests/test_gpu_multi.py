@@ -33,9 +33,15 @@ def test_multi_sweep_matches_per_model_sweeps():
     ms = api.MultiSweep(roms, freqs)
     ms.launch()
     torch.cuda.synchronize()
-    assert int(ms.status.sum().item()) == 0
+    st = ms.status.cpu().numpy()
+    assert set(np.unique(st)) <= {0, 3}
+    # items the FP32 factor cannot refine are flagged and re-solved in FP64
+    flagged = [st[o:o2] == 3 for o, o2 in zip(ms.offsets.cpu().numpy()[:-1], ms.offsets.cpu().numpy()[1:])]
+    flagged = {i: flagged[slot] for slot, i in enumerate(ms.order)}
+    nfix = ms.fixup(roms, freqs)
+    assert nfix == int((st == 3).sum())
     u = np.finfo(np.float64).eps / 2
-    for rm, f, p, spl in zip(roms, freqs, ms.p, ms.spl):
+    for m_i, (rm, f, p, spl) in enumerate(zip(roms, freqs, ms.p, ms.spl)):
         pref, splref = api.rom_sweep(rm, f, batch=16)
         pg, pr = p.cpu().numpy(), pref.cpu().numpy()
         KR, DR, MR = (x.cpu().numpy() for x in (rm.KR, rm.DR, rm.MR))
@@ -44,6 +50,8 @@ def test_multi_sweep_matches_per_model_sweeps():
             A = KR + 1j * w * DR - w * w * MR
             A = A / np.abs(A).max(axis=1, keepdims=True)            # the row equilibration both solvers use
             kappa = np.linalg.cond(A / np.abs(A).max(axis=0, keepdims=True), 1)
+            if flagged[m_i][i]:   # only systems an FP32 factor cannot refine are flagged
+                assert kappa > 1e4, (rm.k, fi, kappa)
             # both are backward stable in FP64 (the multi-model kernel after refinement)
             assert rel(pg[i], pr[i]) <= max(1e-6, 10 * kappa * u), (rm.k, fi, rel(pg[i], pr[i]), kappa)
         assert np.abs(spl.cpu().numpy() - splref.cpu().numpy()).max() <= 1e-4
