@@ -365,10 +365,11 @@ def main():
     B = args.batch
     nsteps = args.warmup + args.steps
 
+    from paper_2310_04734_gb300.sharding import batch_indices
+
     def batch_freqs(step):
         # rank-sharded batches of the 481-point grid (wrapping); each rank sweeps its own frequencies
-        idx = (np.arange(B) + (step * world + rank) * B) % len(freqs)
-        return freqs[idx]
+        return freqs[batch_indices(len(freqs), B, world, rank, step)]
 
     # one workspace serves the device-buffer steps and the host-buffer (e2e) steps
     ws_bytes = max(api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers)),
