@@ -407,7 +407,22 @@ int panel_width(int m) {
 
 template <typename R>
 static int outer_nb() {
-    return sizeof(R) == 4 ? 64 : 32;
+    // FP32: K = 128 per trailing update halves the passes over the trailing matrix
+    return sizeof(R) == 4 ? 128 : 32;
+}
+
+constexpr int kTrsmMaxRows = 64;   // rows of one trsm_kernel launch (its shared-memory triangle)
+
+// U12 = L11^-1 A12 for the nb pivot rows [J, J+nb): triangles of at most kTrsmMaxRows rows,
+// the rows below each updated by a GEMM with the rows just solved.
+template <typename R>
+void blocked_trsm(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int J, int nb, int c0, int c1,
+                  cudaStream_t st) {
+    for (int r = 0; r < nb; r += kTrsmMaxRows) {
+        const int cnt = std::min(kTrsmMaxRows, nb - r);
+        launch_trsm<R>(G, sG, ld, F, J + r, cnt, c0, c1, st);
+        if (r + cnt < nb) launch_gemm_update<R>(G, sG, ld, F, J + r + cnt, J + nb, c0, c1, J + r, cnt, st);
+    }
 }
 
 template <typename R>
@@ -494,7 +509,7 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
         }
         launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);
         if (J + nb < ncols) {
-            launch_trsm<R>(G, sG, ld, F, J, nb, J + nb, ncols, st);
+            blocked_trsm<R>(G, sG, ld, F, J, nb, J + nb, ncols, st);
             trailing_update<R>(G, sG, ld, F, J + nb, m, J + nb, ncols, J, nb, tc_err, st);
         }
     }
