@@ -37,7 +37,7 @@ import workloads as W  # noqa: E402
 REFINE_TOL = 1e-10
 METRIC = "FRF frequencies/sec at <=0.1 dB SPL error vs FP64 full-order sweep; tensor-pipe %"
 UNIT = "frequencies/s"
-GEMM_BYTES_PER_FLOP = 481.7e6 / 16.74e9
+GEMM_BYTES_PER_FLOP = 465.3e6 / 31.35e9
 
 
 def _peaks():
@@ -468,7 +468,7 @@ def main():
                     "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
     else:
         # DRAM bytes per algorithmic flop of the trailing update, from an ncu capture of the
-        # 1640 x 2492 x 64 update of eight config-2 windows (481.7 MB for 16.74 GFLOP); the
+        # 1576 x 2428 x 128 update of eight config-2 windows (465.3 MB for 31.35 GFLOP); the
         # C read-modify-write dominates and scales with the flops at fixed K
         traffic = GEMM_BYTES_PER_FLOP * kern_flops[g] / max(kern_n[g], 1)
         roofline = {"bound": "alu", "kernel": "cgemm_f32_kernel (trailing complex GEMM of the band LU, FP32 SIMT)",
