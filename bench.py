@@ -316,6 +316,63 @@ def run_design(args):
     return 0
 
 
+def run_kernels(args):
+    """FP64 sparse and basis kernels of the path at full size, each timed with CUDA events
+    (on GB300 they are bound by the FP64 pipe rather than HBM): the CSR residual
+    r = F - A(w)X (config 2, 8 frequencies x 4 loads), the Galerkin projection (config 4,
+    160 columns: sparse products and V^H X), and one CGS2-orthonormalised moment build
+    (config 4, one point, 24 moments per load: the basis outgrows L2 after ~36 columns)."""
+    import torch
+    from paper_2310_04734_gb300 import api
+    out = {"mode": "kernels"}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3 / reps
+
+    w2 = W.config2()
+    m2 = api.fsi_assemble(w2.model)
+    F2 = api.dense_loads(w2.model, w2.loads, w2.n_rhs)
+    n2, nnz2, nf = int(m2.dims.n), int(m2.dims.nnz), 8
+    gen = torch.Generator(device="cuda").manual_seed(3)
+    X = torch.randn((nf, n2, w2.n_rhs), dtype=torch.complex128, device="cuda", generator=gen)
+    freqs = w2.freqs_hz[:nf]
+    t = timed(lambda: api.fsi_residual(m2, freqs, X, F2), 5)
+    # per frequency: CSR pattern (4 + 4/row) and values K (16), M (8), D (16) per nonzero, x gathers
+    # (16 per nonzero and column, L2-served), F read and R written (16 each per row and column)
+    byt = nf * (nnz2 * (4 + 16 + 8 + 16) + n2 * 4 + 2 * n2 * w2.n_rhs * 16)
+    out["residual"] = {"ms": t * 1e3, "dram_model_bytes": byt, "GB_s": byt / t / 1e9, "rows": n2, "nnz": nnz2,
+                       "freqs": nf, "loads": w2.n_rhs}
+    del X
+    w4 = W.config4()
+    m4 = api.fsi_assemble(w4.model)
+    F4 = api.dense_loads(w4.model, w4.loads, w4.n_rhs)
+    rcv4 = torch.tensor(api.receiver_dofs(w4.model, w4.receivers), device="cuda")
+    n4, k = int(m4.dims.n), 160
+    # any n x k block has the projection's cost; random columns scaled to unit norm
+    Q = torch.randn((n4, k), dtype=torch.complex128, device="cuda", generator=gen) / np.sqrt(2.0 * n4)
+    t = timed(lambda: api.rom_project(m4, Q, F4, rcv4), 2)
+    out["projection"] = {"ms": t * 1e3, "n": n4, "k": k, "fp64_tflops": 3 * 8.0 * n4 * k * k / t / 1e12}
+    del Q
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    V = api.rom_build(m4, [200.0], 24, F4, kmax=64)
+    torch.cuda.synchronize()
+    out["rom_build"] = {"s": time.perf_counter() - t0, "workload": "config 4, one point at 200 Hz",
+                        "moments_per_load": 24, "k": int(V.shape[1]),
+                        "basis_bytes": int(V.shape[1]) * n4 * 16}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -333,7 +390,7 @@ def main():
     ap.add_argument("--rom-tol", type=float, default=1e-4)
     ap.add_argument("--rom-windows", type=int, default=16)
     ap.add_argument("--design-shifts", type=int, default=16)
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "lu_window", "rom", "design"],
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "lu_window", "rom", "design", "kernels"],
                     help="lu_window: only the batched band-LU of config-2-sized windows (for kernel profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -344,6 +401,8 @@ def main():
         return run_rom(args)
     if args.mode == "design":
         return run_design(args)
+    if args.mode == "kernels":
+        return run_kernels(args)
 
     import torch
     from paper_2310_04734_gb300 import api

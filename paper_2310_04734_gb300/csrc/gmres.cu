@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "csr_rows.cuh"
 #include "engine.h"
 #include "prof.h"
 
@@ -44,46 +45,71 @@ inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
 constexpr int kApR = 8;    // load columns per thread in the operator application
 constexpr int kGrV = 8;    // basis vectors per pass of the Gram kernel
+static_assert(kApR == 8, "column slices of 8, 4, 2 and 1");
 
-// w_p = A^ z_p = rs o (A(w_f) (cs o z_p)) for the active pairs p = f*nrhs + c0 + c,
-// c < nc <= kApR: one thread per (row, frequency) forms each scaled entry once and
-// applies it to every load column, so the matrix is streamed once per frequency.
-__global__ void apply_kernel(DevModel m, const double* omega, const double2* z, double2* w, int nrhs, int c0,
-                             int nc, const int32_t* active) {
+// w_p = A^ z_p = rs o (A(w_f) (cs o z_p)) for the pairs p = f*nrhs + c0 + c, c < R (a power of
+// two), frequency f = blockIdx.y: row groups of kRowLanes lanes form each scaled entry once
+// and apply it to the R columns; after the reduce-scatter each lane writes kept_slots<R>
+// columns of its row (inactive pairs are not written).
+template <int R>
+__global__ void __launch_bounds__(kRowThreads) apply_kernel(DevModel m, const double* omega, const double2* z,
+                                                            double2* w, int nrhs, int c0, const int32_t* active) {
+    constexpr int KS = kept_slots<R>();
     const int f = blockIdx.y;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= m.n) return;
     const int p0 = f * nrhs + c0;
     bool any = false;
 #pragma unroll
-    for (int c = 0; c < kApR; ++c)
-        if (c < nc) any = any || !active || active[p0 + c];
-    if (!any) return;
-    const double om = omega[f];
-    double2 acc[kApR];
+    for (int c = 0; c < R; ++c) any = any || !active || active[p0 + c];
+    if (!any) return;   // uniform over the CTA
+    const double om = omega[f], om2 = om * om, inv_om = 1.0 / om;
+    const int g = threadIdx.x & (kRowLanes - 1);
+    const int s0 = slot_base<R>(g);
+    const bool writer = slot_writer<R>(g);
+    for (int64_t base = int64_t(blockIdx.x) * kRowsPerCta; base < m.n; base += int64_t(gridDim.x) * kRowsPerCta) {
+        const int64_t i = base + threadIdx.x / kRowLanes;
+        const bool valid = i < m.n;
+        double2 acc[R];
 #pragma unroll
-    for (int c = 0; c < kApR; ++c) acc[c] = make_double2(0.0, 0.0);
-    for (int e = m.rowptr[i]; e < m.rowptr[i + 1]; ++e) {
-        const int64_t col = m.col[e];
-        double2 a = a_entry(m, e, om);
-        const double s = col_scale(m, col, om);
-        a.x *= s;
-        a.y *= s;
+        for (int c = 0; c < R; ++c) acc[c] = make_double2(0.0, 0.0);
+        if (valid) {
+            const int e1 = __ldg(m.rowptr + i + 1);
+            for (int e = __ldg(m.rowptr + i) + g; e < e1; e += kRowLanes) {
+                const int64_t col = __ldg(m.col + e);
+                double2 a = a_entry_ld(m, e, om, om2);
+                const double s = col_scale(m, col, om);
+                a.x *= s;
+                a.y *= s;
 #pragma unroll
-        for (int c = 0; c < kApR; ++c)
-            if (c < nc) cfma(acc[c], a, z[int64_t(p0 + c) * m.n + col]);
+                for (int c = 0; c < R; ++c) cfma(acc[c], a, z[int64_t(p0 + c) * m.n + col]);
+            }
+        }
+        group_reduce_scatter<R>(acc, g);
+        if (valid && writer) {
+            const double rs = row_scale_inv(m, i, inv_om);
+#pragma unroll
+            for (int q = 0; q < KS; ++q) {
+                const int c = s0 + q;
+                if (!active || active[p0 + c])
+                    w[int64_t(p0 + c) * m.n + i] = make_double2(rs * acc[q].x, rs * acc[q].y);
+            }
+        }
     }
-    const double rs = row_scale(m, i, om);
-#pragma unroll
-    for (int c = 0; c < kApR; ++c)
-        if (c < nc && (!active || active[p0 + c]))
-            w[int64_t(p0 + c) * m.n + i] = make_double2(rs * acc[c].x, rs * acc[c].y);
 }
 
-// partial[chunk][p][i0 + i] = sum_{q in chunk} conj(V_{i0+i}[p][q]) w[p][q],  i < ni <= kGrV;
-// w is read once per pass for all ni basis vectors
-__global__ void bgram_partial_kernel(const double2* V, int64_t sVb, int64_t n, int nv, int i0, int ni,
+template <int R>
+void apply_launch(const DevModel& m, const double* d_omega, const double2* z, double2* w, int nrhs, int c0, int Fb,
+                  const int32_t* act, cudaStream_t st) {
+    static const int per_sm = resident_ctas(apply_kernel<R>);
+    apply_kernel<R><<<dim3(row_grid_x(m.n, Fb, per_sm), Fb), kRowThreads, 0, st>>>(m, d_omega, z, w, nrhs, c0, act);
+}
+
+// partial[chunk][p][i0 + i] = sum_{q in chunk} conj(V_{i0+i}[p][q]) w[p][q],  i < NI <= kGrV;
+// w is read once per pass for all NI basis vectors (NI a template parameter: a runtime
+// count would leave the unused vectors' DFMAs predicated on the FP64 pipe)
+template <int NI>
+__global__ void bgram_partial_kernel(const double2* V, int64_t sVb, int64_t n, int nv, int i0,
                                      const double2* w, double2* partial, int P, const int32_t* active) {
+    constexpr int ni = NI;
     const int p = blockIdx.x, ch = blockIdx.y;
     if (active && !active[p]) return;
     const int64_t len = (n + kGChunks - 1) / kGChunks;
@@ -127,6 +153,21 @@ __global__ void bgram_reduce_kernel(const double2* partial, int P, int nv, doubl
     double2 s = make_double2(0.0, 0.0);
     for (int ch = 0; ch < kGChunks; ++ch) s = cadd(s, partial[int64_t(ch) * P * nv + q]);
     h[q] = s;
+}
+
+void launch_bgram_partial(const double2* V, int64_t sVb, int64_t n, int nv, int i0, int ni, const double2* w,
+                          double2* partial, int P, const int32_t* act, cudaStream_t st) {
+    const dim3 grid(P, kGChunks);
+    switch (ni) {
+        case 1: bgram_partial_kernel<1><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 2: bgram_partial_kernel<2><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 3: bgram_partial_kernel<3><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 4: bgram_partial_kernel<4><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 5: bgram_partial_kernel<5><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 6: bgram_partial_kernel<6><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        case 7: bgram_partial_kernel<7><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act); break;
+        default: bgram_partial_kernel<8><<<grid, 256, 0, st>>>(V, sVb, n, nv, i0, w, partial, P, act);
+    }
 }
 
 // w[p] -= sum_i V_i[p] h[p][i];  also accumulates |w[p]|^2 into nrm[p] (after the update)
@@ -295,17 +336,25 @@ fsi_status fgmres_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* 
             to_high_kernel<T2><<<cdiv(int64_t(P) * n, 256), 256, 0, st>>>(y, Z + int64_t(j) * sVb, int64_t(P) * n);
             {
                 ProfScope ps(PK_RESID, 0.0, st);
-                for (int c0 = 0; c0 < nrhs; c0 += kApR)
-                    apply_kernel<<<dim3(cdiv(n, 256), Fb), 256, 0, st>>>(m, d_omega, Z + int64_t(j) * sVb, w, nrhs,
-                                                                         c0, std::min(kApR, nrhs - c0), act);
+                const double2* zj = Z + int64_t(j) * sVb;
+                // load columns in power-of-two slices of at most kApR
+                for (int c0 = 0; c0 < nrhs;) {
+                    const int left = nrhs - c0;
+                    const int nc = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+                    switch (nc) {
+                        case 8: apply_launch<8>(m, d_omega, zj, w, nrhs, c0, Fb, act, st); break;
+                        case 4: apply_launch<4>(m, d_omega, zj, w, nrhs, c0, Fb, act, st); break;
+                        case 2: apply_launch<2>(m, d_omega, zj, w, nrhs, c0, Fb, act, st); break;
+                        default: apply_launch<1>(m, d_omega, zj, w, nrhs, c0, Fb, act, st);
+                    }
+                    c0 += nc;
+                }
             }
             // CGS2 against v_0..v_j
             for (int pass = 0; pass < 2; ++pass) {
                 ProfScope ps(PK_RESID, 0.0, st);
                 for (int i0 = 0; i0 <= j; i0 += kGrV)
-                    bgram_partial_kernel<<<dim3(P, kGChunks), 256, 0, st>>>(V, sVb, n, j + 1, i0,
-                                                                            std::min(kGrV, j + 1 - i0), w, part, P,
-                                                                            act);
+                    launch_bgram_partial(V, sVb, n, j + 1, i0, std::min(kGrV, j + 1 - i0), w, part, P, act, st);
                 bgram_reduce_kernel<<<cdiv(int64_t(P) * (j + 1), 256), 256, 0, st>>>(part, P, j + 1, yd);
                 GM_CUDA(cudaMemsetAsync(nrm, 0, sizeof(double) * P, st));
                 bupdate_kernel<<<dim3(cdiv(n, 256), P), 256, 0, st>>>(V, sVb, n, j + 1, yd, w, nrm, act);

@@ -79,13 +79,21 @@ __device__ __forceinline__ T2 cinv(T2 a) {
 // the fluid rows are divided by rho w^2 (reciprocity symmetrisation), then a
 // symmetric Jacobi scaling by |K_ii|^-1/2 is applied.
 __device__ __forceinline__ bool is_fluid(const DevModel& m, int64_t g) { return (g % m.b) < m.npl; }
+// (the fluid/shell test reads the sign bit on the integer pipe: FP64 compares share
+// GB300's narrow FP64 pipe with the arithmetic)
+__device__ __forceinline__ bool neg_bits(double v) { return __double_as_longlong(v) < 0; }
 __device__ __forceinline__ double row_scale(const DevModel& m, int64_t g, double w) {
     const double r = m.rbase[g];   // fluid: 1/(w sqrt(rho |K_ii|)), shell: 1/sqrt(|K_ii|)
-    return r < 0.0 ? -r / w : r;
+    return neg_bits(r) ? -r / w : r;
+}
+// row_scale with 1/w precomputed (a multiply instead of an FP64 divide per row)
+__device__ __forceinline__ double row_scale_inv(const DevModel& m, int64_t g, double inv_w) {
+    const double r = m.rbase[g];
+    return neg_bits(r) ? -r * inv_w : r;
 }
 __device__ __forceinline__ double col_scale(const DevModel& m, int64_t g, double w) {
     const double c = m.cbase[g];   // fluid: w sqrt(rho / |K_ii|), shell: 1/sqrt(|K_ii|)
-    return c < 0.0 ? -c * w : c;
+    return neg_bits(c) ? -c * w : c;
 }
 // A(w)_e = K_e + i w D_e - w^2 M_e
 __device__ __forceinline__ double2 a_entry(const DevModel& m, int64_t e, double w) {

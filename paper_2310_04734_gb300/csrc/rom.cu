@@ -23,6 +23,7 @@
 #include <string>
 #include <vector>
 
+#include "csr_rows.cuh"
 #include "engine.h"
 #include "fsi_internal.h"
 #include "kernels.cuh"
@@ -53,52 +54,73 @@ namespace {
 
 constexpr int kChunks = 64;       // row chunks of the V^H w reductions
 constexpr int kSplit = 16;        // split-K factor of the V^H X projection
+constexpr int kSpC = 4;           // columns per row group in the projection products
 constexpr double kDeflate = 1e-10;
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 
-// y[c] = sum_e (cK K_e + cD D_e + cM M_e) x[c][col_e]  (unscaled, column-major n x nrhs)
-__global__ void spmv_kernel(DevModel m, double2 cK, double2 cD, double2 cM, const double2* x, double2* y, int nrhs,
-                            bool accumulate) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// y[c] = sum_e (cK K_e + cD D_e + cM M_e) x[c][col_e]  (unscaled, column-major n x nrhs),
+// column c = blockIdx.y; row groups of kRowLanes lanes (lane 0 of a group writes)
+__global__ void __launch_bounds__(kRowThreads) spmv_kernel(DevModel m, double2 cK, double2 cD, double2 cM,
+                                                           const double2* x, double2* y, int nrhs, bool accumulate) {
     const int c = blockIdx.y;
-    if (i >= m.n || c >= nrhs) return;
-    double2 acc = make_double2(0.0, 0.0);
+    if (c >= nrhs) return;
+    const int g = threadIdx.x & (kRowLanes - 1);
     const double2* xc = x + c * m.n;
-    for (int e = m.rowptr[i]; e < m.rowptr[i + 1]; ++e) {
-        const double2 k = m.K[e], d = m.D[e];
-        const double mm = m.M[e];
-        double2 a = cmul(cK, k);
-        a = cadd(a, cmul(cD, d));
-        a.x += cM.x * mm;
-        a.y += cM.y * mm;
-        cfma(acc, a, xc[m.col[e]]);
+    for (int64_t base = int64_t(blockIdx.x) * kRowsPerCta; base < m.n; base += int64_t(gridDim.x) * kRowsPerCta) {
+        const int64_t i = base + threadIdx.x / kRowLanes;
+        const bool valid = i < m.n;
+        double2 acc = make_double2(0.0, 0.0);
+        if (valid) {
+            const int e1 = __ldg(m.rowptr + i + 1);
+            for (int e = __ldg(m.rowptr + i) + g; e < e1; e += kRowLanes) {
+                const double2 k = __ldg(m.K + e), d = __ldg(m.D + e);
+                const double mm = __ldg(m.M + e);
+                double2 a = cmul(cK, k);
+                a = cadd(a, cmul(cD, d));
+                a.x = fma(cM.x, mm, a.x);
+                a.y = fma(cM.y, mm, a.y);
+                cfma(acc, a, xc[__ldg(m.col + e)]);
+            }
+        }
+        acc = group_sum(acc);
+        if (valid && g == 0) {
+            if (accumulate) acc = cadd(acc, y[c * m.n + i]);
+            y[c * m.n + i] = acc;
+        }
     }
-    if (accumulate) acc = cadd(acc, y[c * m.n + i]);
-    y[c * m.n + i] = acc;
 }
 
-// partial[chunk][j][c] = sum_{i in chunk} conj(V[i][j]) W[i][c]
+unsigned spmv_grid_x(int64_t n, int ncols) {
+    static const int per_sm = resident_ctas(spmv_kernel);
+    return row_grid_x(n, ncols, per_sm);
+}
+
+// partial[chunk][j][c] = sum_{i in chunk} conj(V[i][j]) W[i][c], c < nrhs <= NR.  NR is a
+// template bound: the column loop is unrolled to NR, and columns at or above nrhs are
+// predicated off but still issue on the FP64 pipe, so the single-column CGS2 of the basis
+// build runs the NR = 1 instance.
+template <int NR>
 __global__ void gram_partial_kernel(const double2* V, int64_t n, int k, const double2* W, int nrhs,
                                     double2* partial) {
     const int j = blockIdx.x, chunk = blockIdx.y;
     const int64_t len = (n + kChunks - 1) / kChunks;
     const int64_t i0 = chunk * len, i1 = min(n, i0 + len);
-    double2 acc[8];
+    double2 acc[NR];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < NR; ++c) acc[c] = make_double2(0.0, 0.0);
     const double2* vj = V + int64_t(j) * n;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const double2 v = vj[i];
         const double2 vc = make_double2(v.x, -v.y);
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < NR; ++c)
             if (c < nrhs) cfma(acc[c], vc, W[c * n + i]);
     }
-    __shared__ double2 red[8][32];
+    __shared__ double2 red[NR][32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
+    for (int c = 0; c < NR; ++c) {
         if (c >= nrhs) break;
         for (int off = 16; off > 0; off >>= 1) {
             acc[c].x += __shfl_down_sync(0xffffffffu, acc[c].x, off);
@@ -123,25 +145,42 @@ __global__ void gram_reduce_kernel(const double2* partial, int k, int nrhs, doub
     H[q] = s;
 }
 
-// W[i][c] -= sum_j V[i][j] H[j][c]
+// W[i][c] -= sum_j V[i][j] H[j][c], c < nrhs <= NR (NR as for gram_partial_kernel)
+template <int NR>
 __global__ void cgs_update_kernel(const double2* V, int64_t n, int k, const double2* H, int nrhs, double2* W) {
     extern __shared__ double2 Hs[];
     for (int q = threadIdx.x; q < k * nrhs; q += blockDim.x) Hs[q] = H[q];
     __syncthreads();
     const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double2 acc[8];
+    double2 acc[NR];
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < NR; ++c) acc[c] = make_double2(0.0, 0.0);
     for (int j = 0; j < k; ++j) {
         const double2 v = V[int64_t(j) * n + i];
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < NR; ++c)
             if (c < nrhs) cfma(acc[c], v, Hs[j * nrhs + c]);
     }
 #pragma unroll
-    for (int c = 0; c < 8; ++c)
+    for (int c = 0; c < NR; ++c)
         if (c < nrhs) W[c * n + i] = csub(W[c * n + i], acc[c]);
+}
+
+void launch_gram_partial(const double2* V, int64_t n, int k, const double2* W, int nrhs, double2* partial,
+                         cudaStream_t st) {
+    if (nrhs == 1)
+        gram_partial_kernel<1><<<dim3(k, kChunks), 256, 0, st>>>(V, n, k, W, nrhs, partial);
+    else
+        gram_partial_kernel<8><<<dim3(k, kChunks), 256, 0, st>>>(V, n, k, W, nrhs, partial);
+}
+
+void launch_cgs_update(const double2* V, int64_t n, int k, const double2* H, int nrhs, double2* W, cudaStream_t st) {
+    const size_t smem = size_t(k) * nrhs * sizeof(double2);
+    if (nrhs == 1)
+        cgs_update_kernel<1><<<cdiv(n, 256), 256, smem, st>>>(V, n, k, H, nrhs, W);
+    else
+        cgs_update_kernel<8><<<cdiv(n, 256), 256, smem, st>>>(V, n, k, H, nrhs, W);
 }
 
 __global__ void sqnorm_kernel(const double2* w, int64_t n, double* out) {
@@ -171,21 +210,56 @@ __global__ void unscale_kernel(DevModel m, double w, const double2* xhat, double
     x[q] = make_double2(s * xhat[q].x, s * xhat[q].y);
 }
 
-// X[j] = A_sel V[j]  for the projection (column j of the n x k product)
-__global__ void spmm_kernel(DevModel m, int which, const double2* V, int k, double2* X) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y;
-    if (i >= m.n) return;
-    const double2* vj = V + int64_t(j) * m.n;
-    double2 acc = make_double2(0.0, 0.0);
-    for (int e = m.rowptr[i]; e < m.rowptr[i + 1]; ++e) {
-        double2 a;
-        if (which == 0) a = m.K[e];
-        else if (which == 1) a = m.D[e];
-        else a = make_double2(m.M[e], 0.0);
-        cfma(acc, a, vj[m.col[e]]);
+// X[j] = A_W V[j] for the projection (A_0 = K, A_1 = D, A_2 = M; columns j = kSpC * blockIdx.y
+// + c, c < kSpC, of the n x k product): each entry is loaded once per group of kSpC columns;
+// after the reduce-scatter each lane writes its kept columns
+template <int W>
+__global__ void __launch_bounds__(kRowThreads) spmm_kernel(DevModel m, const double2* V, int k, double2* X) {
+    constexpr int KS = kept_slots<kSpC>();
+    const int j0 = blockIdx.y * kSpC;
+    const int g = threadIdx.x & (kRowLanes - 1);
+    const int s0 = slot_base<kSpC>(g);
+    const bool writer = slot_writer<kSpC>(g);
+    const bool full = j0 + kSpC <= k;   // uniform over the CTA
+    for (int64_t base = int64_t(blockIdx.x) * kRowsPerCta; base < m.n; base += int64_t(gridDim.x) * kRowsPerCta) {
+        const int64_t i = base + threadIdx.x / kRowLanes;
+        const bool valid = i < m.n;
+        double2 acc[kSpC];
+#pragma unroll
+        for (int c = 0; c < kSpC; ++c) acc[c] = make_double2(0.0, 0.0);
+        if (valid) {
+            const int e1 = __ldg(m.rowptr + i + 1);
+            for (int e = __ldg(m.rowptr + i) + g; e < e1; e += kRowLanes) {
+                const int64_t col = __ldg(m.col + e);
+                const double2 a = W == 0 ? __ldg(m.K + e) : (W == 1 ? __ldg(m.D + e) : make_double2(__ldg(m.M + e), 0.0));
+#pragma unroll
+                for (int c = 0; c < kSpC; ++c) {
+                    // the last column group of a ragged k reads column k - 1 in place of the missing ones
+                    const int jc = full ? j0 + c : min(j0 + c, k - 1);
+                    const double2 v = V[int64_t(jc) * m.n + col];
+                    if (W == 2) {
+                        acc[c].x = fma(a.x, v.x, acc[c].x);
+                        acc[c].y = fma(a.x, v.y, acc[c].y);
+                    } else {
+                        cfma(acc[c], a, v);
+                    }
+                }
+            }
+        }
+        group_reduce_scatter<kSpC>(acc, g);
+        if (valid && writer) {
+#pragma unroll
+            for (int q = 0; q < KS; ++q)
+                if (j0 + s0 + q < k) X[int64_t(j0 + s0 + q) * m.n + i] = acc[q];
+        }
     }
-    X[int64_t(j) * m.n + i] = acc;
+}
+
+template <int W>
+void spmm_launch(const DevModel& m, const double2* V, int k, double2* X, cudaStream_t st) {
+    static const int per_sm = resident_ctas(spmm_kernel<W>);
+    const int ng = int(cdiv(k, kSpC));
+    spmm_kernel<W><<<dim3(row_grid_x(m.n, ng, per_sm), ng), kRowThreads, 0, st>>>(m, V, k, X);
 }
 
 // Split-K tile of C = V^H X: partial[s][a][b] over rows of chunk s (32 x 32 tiles, 256 threads).
@@ -336,9 +410,9 @@ fsi_status sqnorm(const double2* w, int64_t n, double* d_out, double& h_out, cud
 // H = V[:, :k]^H W (nrhs columns), W -= V H
 fsi_status cgs_pass(const double2* V, int64_t n, int k, double2* W, int nrhs, CgsBufs& b, cudaStream_t st) {
     if (k == 0) return FSI_OK;
-    gram_partial_kernel<<<dim3(k, kChunks), 256, 0, st>>>(V, n, k, W, nrhs, b.partial);
+    launch_gram_partial(V, n, k, W, nrhs, b.partial, st);
     gram_reduce_kernel<<<cdiv(int64_t(k) * nrhs, 256), 256, 0, st>>>(b.partial, k, nrhs, b.H);
-    cgs_update_kernel<<<cdiv(n, 256), 256, size_t(k) * nrhs * sizeof(double2), st>>>(V, n, k, b.H, nrhs, W);
+    launch_cgs_update(V, n, k, b.H, nrhs, W, st);
     ROM_LAUNCH();
     return FSI_OK;
 }
@@ -445,8 +519,8 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
         // D has nonzeros only with a floor impedance; probe |D|^2 through a norm of D * ones
         std::vector<double2> ones_h(size_t(n), make_double2(1.0, 0.0));
         ROM_CUDA(cudaMemcpyAsync(w.B, ones_h.data(), sizeof(double2) * n, cudaMemcpyHostToDevice, st));
-        spmv_kernel<<<dim3(cdiv(n, 256), 1), 256, 0, st>>>(m, make_double2(0, 0), make_double2(1, 0),
-                                                            make_double2(0, 0), w.B, w.W, 1, false);
+        spmv_kernel<<<dim3(spmv_grid_x(n, 1), 1), kRowThreads, 0, st>>>(m, make_double2(0, 0), make_double2(1, 0),
+                                                                          make_double2(0, 0), w.B, w.W, 1, false);
         ROM_LAUNCH();
         double dn = 0.0;
         fsi_status s = sqnorm(w.W, n, w.cg.scal, dn, st);
@@ -483,9 +557,9 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                 }
                 nr = k - k0;
                 if (nr > 0 && mom + 1 < q) {
-                    spmv_kernel<<<dim3(cdiv(n, 256), nr), 256, 0, st>>>(m, make_double2(0, 0), make_double2(0, 0),
-                                                                         make_double2(1, 0), V + int64_t(k0) * n,
-                                                                         w.B, nr, false);
+                    spmv_kernel<<<dim3(spmv_grid_x(n, nr), nr), kRowThreads, 0, st>>>(
+                        m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), V + int64_t(k0) * n, w.B, nr,
+                        false);
                     ROM_LAUNCH();
                 }
             }
@@ -506,11 +580,11 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                 int nq = 1;
                 for (int j = 0; j + 1 < q; ++j) {
                     // B = Dt q_j + M p_j ; r = -Kt^-1 B
-                    spmv_kernel<<<dim3(cdiv(n, 256), 1), 256, 0, st>>>(m, make_double2(0, 0), make_double2(1, 0), dt,
-                                                                        w.Qs + int64_t(j) * n, w.B, 1, false);
-                    spmv_kernel<<<dim3(cdiv(n, 256), 1), 256, 0, st>>>(m, make_double2(0, 0), make_double2(0, 0),
-                                                                        make_double2(1, 0), w.Ps + int64_t(j) * n, w.B,
-                                                                        1, true);
+                    spmv_kernel<<<dim3(spmv_grid_x(n, 1), 1), kRowThreads, 0, st>>>(
+                        m, make_double2(0, 0), make_double2(1, 0), dt, w.Qs + int64_t(j) * n, w.B, 1, false);
+                    spmv_kernel<<<dim3(spmv_grid_x(n, 1), 1), kRowThreads, 0, st>>>(
+                        m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), w.Ps + int64_t(j) * n, w.B, 1,
+                        true);
                     ROM_LAUNCH();
                     s = shifted_solve<R>(m, w, om, w.B, 1, max_it, tol, -1.0, w.W, st);
                     if (s != FSI_OK) return s;
@@ -518,12 +592,10 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                     double2* sv = w.X;
                     ROM_CUDA(cudaMemcpyAsync(sv, w.Qs + int64_t(j) * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice,
                                              st));
-                    gram_partial_kernel<<<dim3(nq, kChunks), 256, 0, st>>>(w.Qs, n, nq, w.W, 1, w.cg.partial);
+                    launch_gram_partial(w.Qs, n, nq, w.W, 1, w.cg.partial, st);
                     gram_reduce_kernel<<<cdiv(nq, 256), 256, 0, st>>>(w.cg.partial, nq, 1, w.cg.H);
-                    cgs_update_kernel<<<cdiv(n, 256), 256, size_t(nq) * sizeof(double2), st>>>(w.Qs, n, nq, w.cg.H, 1,
-                                                                                              w.W);
-                    cgs_update_kernel<<<cdiv(n, 256), 256, size_t(nq) * sizeof(double2), st>>>(w.Ps, n, nq, w.cg.H, 1,
-                                                                                              sv);
+                    launch_cgs_update(w.Qs, n, nq, w.cg.H, 1, w.W, st);
+                    launch_cgs_update(w.Ps, n, nq, w.cg.H, 1, sv, st);
                     ROM_LAUNCH();
                     double t2 = 0.0;
                     s = sqnorm(w.W, n, w.cg.scal, t2, st);
@@ -682,14 +754,16 @@ fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64*
     const double2* Vd = reinterpret_cast<const double2*>(V);
     double2* outs[3] = {reinterpret_cast<double2*>(KR), reinterpret_cast<double2*>(DR), reinterpret_cast<double2*>(MR)};
     for (int which = 0; which < 3; ++which) {
-        spmm_kernel<<<dim3(cdiv(n, 256), k), 256, 0, st>>>(m, which, Vd, k, X);
+        if (which == 0) spmm_launch<0>(m, Vd, k, X, st);
+        else if (which == 1) spmm_launch<1>(m, Vd, k, X, st);
+        else spmm_launch<2>(m, Vd, k, X, st);
         vhx_partial_kernel<<<dim3(cdiv(k, 32), cdiv(k, 32), kSplit), 256, 0, st>>>(Vd, X, n, k, part);
         split_reduce_kernel<<<cdiv(int64_t(k) * k, 256), 256, 0, st>>>(part, int64_t(k) * k, outs[which]);
         ROM_LAUNCH();
     }
     // f_R = V^H F (k x nrhs, column-major): H[j][c] layout is row-major k x nrhs -> transpose on copy-out
     double2* H = X;   // reuse
-    gram_partial_kernel<<<dim3(k, kChunks), 256, 0, st>>>(Vd, n, k, reinterpret_cast<const double2*>(F), nrhs, gpart);
+    launch_gram_partial(Vd, n, k, reinterpret_cast<const double2*>(F), nrhs, gpart, st);
     gram_reduce_kernel<<<cdiv(int64_t(k) * nrhs, 256), 256, 0, st>>>(gpart, k, nrhs, H);
     ROM_LAUNCH();
     // explicit transpose (k x nrhs row-major -> column-major)

@@ -31,6 +31,7 @@
 #include <string>
 #include <vector>
 
+#include "csr_rows.cuh"
 #include "engine.h"
 #include "fsi_internal.h"
 #include "kernels.cuh"
@@ -81,24 +82,31 @@ __device__ __forceinline__ double row_weight(const DevModel& m, int64_t i, int s
     return fl ? 1.0 / (m.rho * kd) : 1.0 / kd;
 }
 
-// Y[:, 3j + w] = A_w V[:, j] for j in [j0, j0 + nj), A_0 = K, A_1 = D, A_2 = M (one pass over each row)
-__global__ void yspmm_kernel(DevModel m, const double2* V, int j0, double2* Y) {
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+// Y[:, 3j + w] = A_w V[:, j] for j in [j0, j0 + nj), A_0 = K, A_1 = D, A_2 = M (one pass over
+// each row, j = j0 + blockIdx.y); row groups of kRowLanes lanes, lanes 0..2 of a group write
+__global__ void __launch_bounds__(kRowThreads) yspmm_kernel(DevModel m, const double2* V, int j0, double2* Y) {
     const int j = j0 + blockIdx.y;
-    if (i >= m.n) return;
+    const int g = threadIdx.x & (kRowLanes - 1);
     const double2* vj = V + int64_t(j) * m.n;
-    double2 yk = make_double2(0.0, 0.0), yd = yk, ym = yk;
-    for (int e = m.rowptr[i]; e < m.rowptr[i + 1]; ++e) {
-        const double2 x = vj[m.col[e]];
-        cfma(yk, m.K[e], x);
-        cfma(yd, m.D[e], x);
-        const double mm = m.M[e];
-        ym.x += mm * x.x;
-        ym.y += mm * x.y;
+    for (int64_t base = int64_t(blockIdx.x) * kRowsPerCta; base < m.n; base += int64_t(gridDim.x) * kRowsPerCta) {
+        const int64_t i = base + threadIdx.x / kRowLanes;
+        const bool valid = i < m.n;
+        double2 y[4] = {make_double2(0.0, 0.0), make_double2(0.0, 0.0), make_double2(0.0, 0.0),
+                        make_double2(0.0, 0.0)};   // slot 3 unused (power-of-two reduce-scatter)
+        if (valid) {
+            const int e1 = __ldg(m.rowptr + i + 1);
+            for (int e = __ldg(m.rowptr + i) + g; e < e1; e += kRowLanes) {
+                const double2 x = vj[__ldg(m.col + e)];
+                cfma(y[0], __ldg(m.K + e), x);
+                cfma(y[1], __ldg(m.D + e), x);
+                const double mm = __ldg(m.M + e);
+                y[2].x = fma(mm, x.x, y[2].x);
+                y[2].y = fma(mm, x.y, y[2].y);
+            }
+        }
+        group_reduce_scatter<4>(y, g);   // lane g now holds slot g (kRowLanes = 4)
+        if (valid && g < 3) Y[(int64_t(3) * j + g) * m.n + i] = y[0];
     }
-    Y[(int64_t(3) * j + 0) * m.n + i] = yk;
-    Y[(int64_t(3) * j + 1) * m.n + i] = yd;
-    Y[(int64_t(3) * j + 2) * m.n + i] = ym;
 }
 
 // partial[s][b][a] = sum_{i in split s} w(i) conj(A[i][a0 + a]) B[i][b0 + b]   (32 x 32 output tiles)
@@ -302,7 +310,8 @@ fsi_status grow_gram(const DevModel& m, GreedyWS& w, const double2* V, const dou
                      cudaStream_t st) {
     if (k1 <= k0) return FSI_OK;
     const int64_t n = m.n;
-    yspmm_kernel<<<dim3(cdiv(n, 256), k1 - k0), 256, 0, st>>>(m, V, k0, w.Y);
+    static const int per_sm = resident_ctas(yspmm_kernel);
+    yspmm_kernel<<<dim3(row_grid_x(n, k1 - k0, per_sm), k1 - k0), kRowThreads, 0, st>>>(m, V, k0, w.Y);
     GR_CUDA(cudaGetLastError());
     // P = V^H Y: new columns of Y against all of V, and new rows of V against the old columns of Y
     fsi_status s = wgram(m, 0, V, 0, k1, w.Y, 3 * k0, 3 * (k1 - k0), w.part, w.P, w.ldp, 0, 3 * k0, 0, st);

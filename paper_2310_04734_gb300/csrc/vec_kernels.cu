@@ -4,6 +4,7 @@
 // the low-precision correction, and the receiver read-out with SPL.
 #include <cmath>
 
+#include "csr_rows.cuh"
 #include "kernels.cuh"
 #include "prof.h"
 
@@ -11,79 +12,116 @@ namespace fsi {
 
 namespace {
 
-constexpr int kResRmax = 8;
 
-__global__ void residual_kernel(DevModel m, const double* omega, double omega0, const double2* x, int64_t sX,
-                                const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms, int nstride,
-                                int ncol0, bool scaled, double* absn) {
+// r_c = rs o (f_c - A(w) (cs o x_c)) (scaled) or f_c - A(w) x_c for the R load columns of
+// this launch (R a power of two), frequency f = blockIdx.y; norms[f][ncol0 + c] += |r_c|^2
+// and, with absn, absn[f][ncol0 + c] += |rs o (|A| |cs o x_c| + |f_c|)|^2 (the rounding
+// level of the residual).  Row groups of kRowLanes lanes; after the reduce-scatter each
+// lane owns kept_slots<R> load columns of its row.
+template <int R, bool scaled>
+__global__ void __launch_bounds__(kRowThreads) residual_kernel(DevModel m, const double* omega, double omega0,
+                                                               const double2* x, int64_t sX, const double2* Fm,
+                                                               double2* r, int64_t sR, double* norms, int nstride,
+                                                               int ncol0, double* absn) {
+    constexpr int KS = kept_slots<R>();
     const int f = blockIdx.y;
-    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-    const double w = omega ? omega[f] : omega0;
-    double2 acc[kResRmax];
+    const double w = omega ? omega[f] : omega0, w2 = w * w, inv_w = 1.0 / w;
+    const int g = threadIdx.x & (kRowLanes - 1);
+    const int c0 = slot_base<R>(g);
+    const bool writer = slot_writer<R>(g);
+    const double2* xf = x ? x + f * sX : nullptr;
+    double2* rf = r + f * sR;
+    double nrm[KS], anr[KS];
 #pragma unroll
-    for (int c = 0; c < kResRmax; ++c) acc[c] = make_double2(0.0, 0.0);
-    double nrm[kResRmax], sab[kResRmax], anr[kResRmax];
+    for (int q = 0; q < KS; ++q) nrm[q] = anr[q] = 0.0;
+    for (int64_t base = int64_t(blockIdx.x) * kRowsPerCta; base < m.n; base += int64_t(gridDim.x) * kRowsPerCta) {
+        const int64_t i = base + threadIdx.x / kRowLanes;
+        const bool valid = i < m.n;
+        double2 acc[R];
+        double sab[R];
 #pragma unroll
-    for (int c = 0; c < kResRmax; ++c) nrm[c] = sab[c] = anr[c] = 0.0;
-    if (i < m.n) {
-        if (x) {
-            const double2* xf = x + f * sX;
-            const int e1 = m.rowptr[i + 1];
-            for (int e = m.rowptr[i]; e < e1; ++e) {
-                const int64_t col = m.col[e];
-                double2 a = a_entry(m, e, w);
+        for (int c = 0; c < R; ++c) {
+            acc[c] = make_double2(0.0, 0.0);
+            sab[c] = 0.0;
+        }
+        if (valid && xf) {
+            const int e1 = __ldg(m.rowptr + i + 1);
+            for (int e = __ldg(m.rowptr + i) + g; e < e1; e += kRowLanes) {
+                const int64_t col = __ldg(m.col + e);
+                double2 a = a_entry_ld(m, e, w, w2);
                 if (scaled) {
                     const double s = col_scale(m, col, w);
                     a.x *= s;
                     a.y *= s;
                 }
 #pragma unroll
-                for (int c = 0; c < kResRmax; ++c)
-                    if (c < nrhs) cfma(acc[c], a, xf[c * m.n + col]);
+                for (int c = 0; c < R; ++c) cfma(acc[c], a, xf[c * m.n + col]);
                 if (absn) {
                     const double aa = hypot(a.x, a.y);
 #pragma unroll
-                    for (int c = 0; c < kResRmax; ++c)
-                        if (c < nrhs) {
-                            const double2 xv = xf[c * m.n + col];
-                            sab[c] += aa * hypot(xv.x, xv.y);
-                        }
+                    for (int c = 0; c < R; ++c) {
+                        const double2 xv = xf[c * m.n + col];
+                        sab[c] = fma(aa, hypot(xv.x, xv.y), sab[c]);
+                    }
                 }
             }
         }
-        const double rs = scaled ? row_scale(m, i, w) : 1.0;
-        double2* rf = r + f * sR;
+        group_reduce_scatter<R>(acc, g);
+        if (absn) group_reduce_scatter<R>(sab, g);
+        if (valid && writer) {
+            const double rs = scaled ? row_scale_inv(m, i, inv_w) : 1.0;
 #pragma unroll
-        for (int c = 0; c < kResRmax; ++c) {
-            if (c >= nrhs) break;
-            const double2 fv = Fm[c * m.n + i];
-            const double2 v = make_double2(rs * (fv.x - acc[c].x), rs * (fv.y - acc[c].y));
-            rf[c * m.n + i] = v;
-            nrm[c] = v.x * v.x + v.y * v.y;
-            const double t = rs * (sab[c] + hypot(fv.x, fv.y));
-            anr[c] = t * t;
+            for (int q = 0; q < KS; ++q) {
+                const int c = c0 + q;
+                const double2 fv = Fm[c * m.n + i];
+                const double2 v = make_double2(rs * (fv.x - acc[q].x), rs * (fv.y - acc[q].y));
+                rf[c * m.n + i] = v;
+                nrm[q] = fma(v.x, v.x, fma(v.y, v.y, nrm[q]));
+                if (absn) {
+                    const double t = rs * (sab[q] + hypot(fv.x, fv.y));
+                    anr[q] = fma(t, t, anr[q]);
+                }
+            }
         }
     }
-    if (absn) {
-        const int lane = threadIdx.x & 31;
+    // per load column: shared-memory sums over the CTA, then one global atomic per column
+    __shared__ double red[2][R];
+    if (threadIdx.x < 2 * R) (&red[0][0])[threadIdx.x] = 0.0;
+    __syncthreads();
+    if (writer) {
 #pragma unroll
-        for (int c = 0; c < kResRmax; ++c) {
-            if (c >= nrhs) break;
-            double v = anr[c];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0 && v != 0.0) atomicAdd(&absn[f * nstride + ncol0 + c], v);
+        for (int q = 0; q < KS; ++q) {
+            if (nrm[q] != 0.0) atomicAdd(&red[0][c0 + q], nrm[q]);
+            if (anr[q] != 0.0) atomicAdd(&red[1][c0 + q], anr[q]);
         }
     }
-    if (norms) {
-        const int lane = threadIdx.x & 31;
-#pragma unroll
-        for (int c = 0; c < kResRmax; ++c) {
-            if (c >= nrhs) break;
-            double v = nrm[c];
-            for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-            if (lane == 0 && v != 0.0) atomicAdd(&norms[f * nstride + ncol0 + c], v);
-        }
+    __syncthreads();
+    if (threadIdx.x < R) {
+        const int c = threadIdx.x;
+        if (norms && red[0][c] != 0.0) atomicAdd(&norms[f * nstride + ncol0 + c], red[0][c]);
+        if (absn && red[1][c] != 0.0) atomicAdd(&absn[f * nstride + ncol0 + c], red[1][c]);
     }
+}
+
+template <int R, bool scaled>
+void residual_launch_s(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
+                       const double2* Fm, double2* r, int64_t sR, double* norms, int nstride, int c0, double* absn,
+                       cudaStream_t st) {
+    static const int per_sm = resident_ctas(residual_kernel<R, scaled>);
+    const dim3 grid(row_grid_x(m.n, F, per_sm), F);
+    residual_kernel<R, scaled><<<grid, kRowThreads, 0, st>>>(m, d_omega, omega0, x ? x + c0 * m.n : nullptr, sX,
+                                                             Fm + c0 * m.n, r + c0 * m.n, sR, norms, nstride, c0,
+                                                             absn);
+}
+
+template <int R>
+void residual_launch(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
+                     const double2* Fm, double2* r, int64_t sR, double* norms, int nstride, int c0, bool scaled,
+                     double* absn, cudaStream_t st) {
+    if (scaled)
+        residual_launch_s<R, true>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nstride, c0, absn, st);
+    else
+        residual_launch_s<R, false>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nstride, c0, absn, st);
 }
 
 template <typename T2>
@@ -138,12 +176,18 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return unsigned((a + b - 1) / b
 void launch_residual(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
                      const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms, bool scaled,
                      cudaStream_t st, double* absn) {
-    for (int c0 = 0; c0 < nrhs; c0 += kResRmax) {
-        const int nc = nrhs - c0 < kResRmax ? nrhs - c0 : kResRmax;
-        dim3 grid(ceil_div(m.n, 256), F);
-        ProfScope ps(PK_RESID, 0.0, st);
-        residual_kernel<<<grid, 256, 0, st>>>(m, d_omega, omega0, x ? x + c0 * m.n : nullptr, sX, Fm + c0 * m.n, nc,
-                                              r + c0 * m.n, sR, norms, nrhs, c0, scaled, absn);
+    ProfScope ps(PK_RESID, 0.0, st);
+    // load columns in power-of-two slices of at most 8
+    for (int c0 = 0; c0 < nrhs;) {
+        const int left = nrhs - c0;
+        const int nc = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
+        switch (nc) {
+            case 8: residual_launch<8>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            case 4: residual_launch<4>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            case 2: residual_launch<2>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            default: residual_launch<1>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st);
+        }
+        c0 += nc;
     }
 }
 

@@ -133,19 +133,27 @@ def test_minimal_slab_count():
     assert (_per_freq_rel(res.p.cpu().numpy(), y) <= _fp64_bound(_dense_kappa(asm, freqs))).all()
 
 
-def test_residual_kernel_matches_sparse_product():
+@pytest.mark.parametrize("ncols", [None, 1, 3, 8, 13])
+def test_residual_kernel_matches_sparse_product(ncols):
+    """The CSR residual against scipy's sparse product; the column counts cover every
+    power-of-two column slice of the kernel (13 = 8 + 4 + 1, 3 = 2 + 1)."""
     torch = need_cuda()
     w = W.small_model(floor=True)
     api, model, F, rcv = _setup(w)
     asm = fem.assemble(w.model)
     rng = np.random.default_rng(11)
-    freqs = [40.0, 90.0]
-    X = rng.standard_normal((2, asm.n, w.n_rhs)) + 1j * rng.standard_normal((2, asm.n, w.n_rhs))
+    if ncols is not None:
+        Fh = rng.standard_normal((asm.n, ncols)) + 1j * rng.standard_normal((asm.n, ncols))
+        F = torch.tensor(Fh, device="cuda")
+    nc = F.shape[1]
+    freqs = [40.0, 90.0, 333.0]
+    X = rng.standard_normal((3, asm.n, nc)) + 1j * rng.standard_normal((3, asm.n, nc))
     R = api.fsi_residual(model, freqs, torch.tensor(X, device="cuda"), F).cpu().numpy()
     Fh = F.cpu().numpy()
     for i, f in enumerate(freqs):
         ref = Fh - asm.A(2 * np.pi * f) @ X[i]
-        assert rel(R[i], ref) <= 1e-13
+        for c in range(nc):
+            assert rel(R[i][:, c], ref[:, c]) <= 1e-13
 
 
 @pytest.mark.parametrize("precision", ["fp32_ir", "tf32x3_ir"])
