@@ -150,3 +150,34 @@ def test_windows_partition_the_band_and_bisect_above_tolerance():
     for win in wins:
         npts = sum(1 for c in cand if win["lo"] <= c <= win["hi"])
         assert win["maxest"] <= 1e-6 or npts < 6 or len(wins) == 4
+
+
+def test_projection_needs_fp64_accuracy():
+    """Why the Galerkin projection stays in FP64 (Sec. 3.3, Eq. 11): normwise
+    perturbations of K_R, D_R, M_R at the accuracy of a split-precision tensor-core
+    product (2^-21, three TF32 products) move the reduced outputs of the config-1 model
+    by far more than 0.1 dB, while FP64-level perturbations do not."""
+    import copy
+    w = W.config1()
+    asm = fem.assemble(w.model)
+    F = fem.load_matrix(w.model, w.loads, w.n_rhs)
+    rc = fem.receiver_dofs(w.model, w.receivers)
+    V = rom.build_basis(asm, [40.0, 90.0, 140.0, 185.0], 8, F, 200)
+    rm = rom.project(asm, V, F, rc)
+    freqs = np.arange(20.0, 200.5, 1.0)
+    y0 = rom.reduced_sweep(rm, freqs)
+    rng = np.random.default_rng(0)
+
+    def worst_db(eps):
+        r2 = copy.copy(rm)
+        for attr in ("KR", "DR", "MR"):
+            A = getattr(rm, attr)
+            if np.abs(A).max() == 0:
+                continue
+            E = rng.standard_normal(A.shape) + 1j * rng.standard_normal(A.shape)
+            setattr(r2, attr, A + E * (eps * np.linalg.norm(A, 2) / np.linalg.norm(E, 2)))
+        y = rom.reduced_sweep(r2, freqs)
+        return float(np.abs(20.0 * np.log10(np.abs(y) / np.abs(y0))).max())
+
+    assert worst_db(2.0 ** -53) < 1e-6
+    assert worst_db(2.0 ** -21) > 0.1
