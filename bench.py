@@ -259,11 +259,12 @@ def run_design(args):
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     t0 = time.perf_counter()
-    roms, handles = [], []
+    roms, handles, bases = [], [], []
     for i, w in enumerate(variants):
         g, h = ds.variant_rom(w, q, kmax, args.design_shifts, 1e-4, mlp_params=st.params if i >= 16 else None)
         roms.append(g.rom)
         handles.append(h)
+        bases.append(g.V)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     ms = api.MultiSweep(roms, [w.freqs_hz for w in variants])
@@ -293,9 +294,12 @@ def run_design(args):
     # reduced systems the FP32 factor could not refine are re-solved in FP64 (not timed)
     nfix = ms.fixup(roms, [w.freqs_hz for w in variants])
     # checks at 40 seeded frequencies per variant
-    worst, resolve, kk = [], 0, []
+    worst, resolve, kk, resid = [], 0, [], []
     for i, w in enumerate(variants):
         idx = np.sort(np.random.default_rng([w.config_id, 3]).choice(len(w.freqs_hz), size=40, replace=False))
+        # FP64 full-order residual of the lifted reduced solutions (CSR residual kernel)
+        model_i, F_i, _ = handles[i]
+        resid.append(float(api.rom_residual_check(model_i, bases[i], roms[i], F_i, w.freqs_hz[idx]).max()))
         db, _ = ds.check_variant(w, handles[i], ms.p[i], idx)
         worst.append(float(db.max()))
         resolve += int((db > 0.1).sum())
@@ -307,6 +311,7 @@ def run_design(args):
         "sweep_ms": t_sweep * 1e3, "train_s": t_train, "build_s": t_build, "fp64_resolved_reduced": nfix,
         "estimator_final_loss": float(np.mean(losses[-100:])), "k": {"min": min(kk), "max": max(kk)},
         "check": {"frequencies": 40 * len(variants), "resolved_full_order": resolve,
+                  "max_full_residual": float(max(resid)), "median_variant_max_full_residual": float(np.median(resid)),
                   "max_spl_err_db_residual_driven": float(worst[:16].max()),
                   "max_spl_err_db_estimator_driven": float(worst[16:].max()),
                   "median_worst_db_residual_driven": float(np.median(worst[:16])),

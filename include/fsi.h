@@ -268,6 +268,24 @@ fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64*
                      const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
                      fsi_c64* p_out, double* spl_out, void* stream);
 
+/* Workspace bytes for rom_residual_check (batch frequencies at a time). */
+fsi_status rom_residual_check_workspace(const fsi_dims* dims, int k, int nrhs, int batch, size_t* bytes);
+
+/* Full-order FP64 residual of reduced solutions (the check of Sec. 3.3's error
+ * measure by the residual, Sec. 5): for each frequency w = 2 pi f_hz[i] the reduced
+ * system (K_R + i w D_R - w^2 M_R) x_R = f_R is solved as in rom_sweep, lifted to
+ * x = V x_R and checked with the CSR residual of the full model:
+ *   relres[i][c] = |f_c - A(w) x_c|_2 / |f_c|_2   (unscaled, FP64).
+ * V: n x k column-major device basis the reduced matrices were projected with;
+ * KR/DR/MR/fR as rom_project writes them (device, column-major); F: n x nrhs
+ * column-major device loads; f_hz host; relres host [nf][nrhs].  nrhs <= 8.
+ * Errors: FSI_EINVAL (sizes, small workspace), FSI_ESINGULAR (reduced system). */
+fsi_status rom_residual_check(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k,
+                              const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR,
+                              const fsi_c64* fR, const fsi_c64* F, int nrhs, const double* f_hz,
+                              int nf, int batch, void* ws, size_t ws_bytes, double* relres,
+                              void* stream);
+
 /* Greedy expansion points (paper Sec. 3.3; its error measure replaced by a
  * residual estimate, as Sec. 5 suggests).  Options: */
 typedef struct {

@@ -178,6 +178,20 @@ def residual_estimate(asm, V, rm: ReducedModel, F, freqs_hz) -> np.ndarray:
     return out
 
 
+def full_residual(asm, V, rm: ReducedModel, F, freqs_hz) -> np.ndarray:
+    """Plain relative residual of the lifted reduced solution in the full model, per load
+    column: ||f_c - A(w) V x_R,c||_2 / ||f_c||_2 with A(w) = K + i w D - w^2 M (Eq. 8) and
+    x_R the reduced solution (Eq. 11).  Shape [len(freqs_hz)][n_columns]."""
+    out = np.empty((len(freqs_hz), F.shape[1]))
+    fn = np.linalg.norm(F, axis=0)
+    for i, f in enumerate(freqs_hz):
+        om = 2.0 * np.pi * f
+        AR = rm.KR + 1j * om * rm.DR - om ** 2 * rm.MR
+        x = V @ np.linalg.solve(AR, rm.fR)
+        out[i] = np.linalg.norm(F - asm.A(om) @ x, axis=0) / fn
+    return out
+
+
 def greedy(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts: int,
            initial_hz: Optional[List[float]] = None):
     """Greedy expansion points: add the candidate with the largest residual estimate.

@@ -100,6 +100,10 @@ SIGNATURES = {
     "rom_sweep_workspace": (c_int, [c_int, c_int, c_int, c_int, C.POINTER(c_size_t)]),
     "rom_sweep": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
                           c_double_p, c_int, c_int, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+    "rom_residual_check_workspace": (c_int, [C.POINTER(fsi_dims), c_int, c_int, c_int, C.POINTER(c_size_t)]),
+    "rom_residual_check": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                   c_void_p, c_void_p, c_int, c_double_p, c_int, c_int, c_void_p, c_size_t,
+                                   c_double_p, c_void_p]),
     "rom_greedy_workspace": (c_int, [C.POINTER(fsi_dims), c_int, C.POINTER(fsi_greedy_opts),
                                      C.POINTER(c_size_t)]),
     "rom_greedy": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_double_p, c_int, c_double_p,

@@ -324,6 +324,31 @@ def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256):
     return p, spl
 
 
+def rom_residual_check(model: DeviceModel, V, rom: DeviceROM, F, freqs_hz, batch: int = 16) -> np.ndarray:
+    """Full-order FP64 residual |f - A(w) V x_R| / |f| of the reduced solutions at the given
+    frequencies, per load column ([nf][nrhs] host array). V: the n x k basis rom was projected with."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    k = rom.k
+    nrhs = int(F.shape[1])
+    cm = lambda X: X.t().contiguous()
+    KR, DR, MR, fR = cm(rom.KR), cm(rom.DR), cm(rom.MR), cm(rom.fR)
+    Vc, Fc = cm(V), cm(F)
+    bt = min(batch, nf)
+    need = C.c_size_t()
+    L.check(lib.rom_residual_check_workspace(C.byref(model.dims), k, nrhs, bt, C.byref(need)),
+            "rom_residual_check_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    out = np.empty((nf, nrhs), np.float64)
+    L.check(lib.rom_residual_check(C.byref(model.dims), _ptr(model.buf), _ptr(Vc), k, _ptr(KR), _ptr(DR), _ptr(MR),
+                                   _ptr(fR), _ptr(Fc), nrhs, f.ctypes.data_as(L.c_double_p), nf, bt, _ptr(ws),
+                                   C.c_size_t(need.value), out.ctypes.data_as(L.c_double_p), _stream_ptr()),
+            "rom_residual_check")
+    return out
+
+
 @dataclass
 class GreedyResult:
     V: object            # n x k basis (torch, device)

@@ -91,6 +91,36 @@ __global__ void __launch_bounds__(kRowThreads) spmv_kernel(DevModel m, double2 c
     }
 }
 
+// Back-projection of a batch of reduced solutions: x[f][c][i] = sum_j V[i][j] x_R[f][j][c] with
+// x_R[f][j][c] = cs[f*k + j] G[f*k*(k+nrhs) + j*(k+nrhs) + k + c] (the equilibrated reduced
+// solve's layout); frequency f = blockIdx.y, one thread per row, columns c < nrhs <= NR
+template <int NR>
+__global__ void backproject_kernel(const double2* V, int64_t n, int k, const double2* G, const double* cs, int nrhs,
+                                   double2* x) {
+    const int f = blockIdx.y;
+    const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ld = k + nrhs;
+    const double2* Gf = G + int64_t(f) * k * ld;
+    const double* csf = cs + int64_t(f) * k;
+    double2 acc[NR];
+#pragma unroll
+    for (int c = 0; c < NR; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int j = 0; j < k; ++j) {
+        const double2 v = V[int64_t(j) * n + i];
+        const double s = __ldg(csf + j);
+#pragma unroll
+        for (int c = 0; c < NR; ++c)
+            if (c < nrhs) {
+                const double2 g = __ldg(Gf + int64_t(j) * ld + k + c);
+                cfma(acc[c], v, make_double2(s * g.x, s * g.y));
+            }
+    }
+#pragma unroll
+    for (int c = 0; c < NR; ++c)
+        if (c < nrhs) x[(int64_t(f) * nrhs + c) * n + i] = acc[c];
+}
+
 unsigned spmv_grid_x(int64_t n, int ncols) {
     static const int per_sm = resident_ctas(spmv_kernel);
     return row_grid_x(n, ncols, per_sm);
@@ -803,6 +833,68 @@ fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64*
         if (s != FSI_OK) return s;
     }
     ROM_CUDA(cudaStreamSynchronize(st));
+    return FSI_OK;
+}
+
+fsi_status rom_residual_check_workspace(const fsi_dims* dims, int k, int nrhs, int batch, size_t* bytes) {
+    ROM_REQUIRE(dims && bytes && k > 0 && nrhs > 0 && nrhs <= 8 && batch > 0, "bad residual check workspace arguments");
+    const size_t vec = size_t(batch) * nrhs * dims->n * sizeof(double2);
+    *bytes = reduced_solve_ws(k, nrhs, batch) + 2 * vec + size_t(batch + 1) * nrhs * sizeof(double) + 6 * 256;
+    return FSI_OK;
+}
+
+fsi_status rom_residual_check(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k, const fsi_c64* KR,
+                              const fsi_c64* DR, const fsi_c64* MR, const fsi_c64* fR, const fsi_c64* F, int nrhs,
+                              const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes, double* relres,
+                              void* stream) {
+    ROM_REQUIRE(dims && d_model && V && KR && DR && MR && fR && F && f_hz && ws && relres, "NULL argument");
+    ROM_REQUIRE(k > 0 && k <= dims->n && nrhs > 0 && nrhs <= 8 && nf > 0 && batch > 0, "bad residual check sizes");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const DevModel m = dev_model(*dims, d_model);
+    const int64_t n = dims->n;
+    const int bt = std::min(batch, nf);
+    const size_t red = (reduced_solve_ws(k, nrhs, bt) + 255) & ~size_t(255);
+    Carver c(static_cast<char*>(ws) + red, ws_bytes > red ? ws_bytes - red : 0);
+    double2* x = c.take<double2>(size_t(bt) * nrhs * n);
+    double2* r = c.take<double2>(size_t(bt) * nrhs * n);
+    double* norms = c.take<double>(size_t(bt) * nrhs);
+    double* fn = c.take<double>(nrhs);
+    ROM_REQUIRE(c.fits() && ws_bytes >= red, "residual check workspace too small");
+    const double2* Fd = reinterpret_cast<const double2*>(F);
+    // |f_c|^2: the residual kernel with no iterate
+    ROM_CUDA(cudaMemsetAsync(fn, 0, sizeof(double) * nrhs, st));
+    launch_residual(m, nullptr, 1.0, 1, nullptr, 0, Fd, nrhs, r, 0, fn, false, st);
+    std::vector<double> hfn(nrhs), hn(size_t(bt) * nrhs);
+    ROM_CUDA(cudaMemcpyAsync(hfn.data(), fn, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st));
+    for (int f0 = 0; f0 < nf; f0 += bt) {
+        const int Fb = std::min(bt, nf - f0);
+        ReducedBatch rb;
+        fsi_status s = reduced_solve_batch(k, reinterpret_cast<const double2*>(KR), reinterpret_cast<const double2*>(DR),
+                                           reinterpret_cast<const double2*>(MR), reinterpret_cast<const double2*>(fR),
+                                           nrhs, f_hz + f0, Fb, ws, red, rb, st);
+        if (s != FSI_OK) return s;
+        const dim3 grid(cdiv(n, 256), Fb);
+        const double2* Vd = reinterpret_cast<const double2*>(V);
+        if (nrhs == 1)
+            backproject_kernel<1><<<grid, 256, 0, st>>>(Vd, n, k, rb.G, rb.cs, nrhs, x);
+        else if (nrhs == 2)
+            backproject_kernel<2><<<grid, 256, 0, st>>>(Vd, n, k, rb.G, rb.cs, nrhs, x);
+        else if (nrhs <= 4)
+            backproject_kernel<4><<<grid, 256, 0, st>>>(Vd, n, k, rb.G, rb.cs, nrhs, x);
+        else
+            backproject_kernel<8><<<grid, 256, 0, st>>>(Vd, n, k, rb.G, rb.cs, nrhs, x);
+        ROM_LAUNCH();
+        ROM_CUDA(cudaMemsetAsync(norms, 0, sizeof(double) * Fb * nrhs, st));
+        launch_residual(m, rb.omega, 0.0, Fb, x, int64_t(nrhs) * n, Fd, nrhs, r, int64_t(nrhs) * n, norms, false,
+                        st);
+        ROM_LAUNCH();
+        ROM_CUDA(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
+        ROM_CUDA(cudaStreamSynchronize(st));
+        for (int q = 0; q < Fb * nrhs; ++q) {
+            const double d = hfn[q % nrhs];
+            relres[int64_t(f0) * nrhs + q] = d > 0 ? std::sqrt(hn[q] / d) : 0.0;
+        }
+    }
     return FSI_OK;
 }
 

@@ -44,6 +44,35 @@ def test_rom_matches_oracle_rom(floor):
     assert rom.relative_error(y, pg[idx]).max() < 1e-5
 
 
+@pytest.mark.parametrize("floor", [False, True])
+def test_rom_residual_check_matches_oracle(floor):
+    """FP64 full-order residual of the lifted reduced solutions (CSR residual kernel)
+    against the oracle's explicit residual with its own basis of the same Krylov space;
+    batch 3 over 7 frequencies leaves a ragged last batch."""
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    w = W.small_model(floor=floor)
+    spec = w.model
+    shifts = [60.0, 150.0, 250.0]
+    q = 3
+    model = api.fsi_assemble(spec)
+    F = api.dense_loads(spec, w.loads, w.n_rhs)
+    rcv = torch.tensor(api.receiver_dofs(spec, w.receivers), device="cuda")
+    V = api.rom_build(model, shifts, q, F, kmax=200, precision="fp32_ir", tol=1e-12, max_refine=30)
+    rm = api.rom_project(model, V, F, rcv)
+    freqs = np.array([45.0, 60.0, 100.0, 150.0, 200.0, 250.0, 280.0])
+    got = api.rom_residual_check(model, V, rm, F, freqs, batch=3)
+    asm = fem.assemble(spec)
+    Fo = fem.load_matrix(spec, w.loads, w.n_rhs)
+    Vo = rom.build_basis(asm, shifts, q, Fo, 200)
+    ref = rom.full_residual(asm, Vo, rom.project(asm, Vo, Fo, fem.receiver_dofs(spec, w.receivers)), Fo, freqs)
+    assert got.shape == ref.shape
+    # residuals span many decades; at the expansion points both sit at the reduced solve's rounding
+    assert np.all(np.abs(got - ref) <= 1e-3 * ref + 1e-6), (got, ref)
+    idx = [list(freqs).index(s) for s in shifts]
+    assert got[idx].max() < 1e-5
+
+
 def test_projection_matches_oracle_matrices():
     torch = need_cuda()
     from paper_2310_04734_gb300 import api
