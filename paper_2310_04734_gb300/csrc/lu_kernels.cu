@@ -214,6 +214,34 @@ __global__ void __launch_bounds__(kTrsmThreads) trsm_kernel(T2* G, int64_t sG, i
     for (int i = 1; i < cnt; ++i) A[int64_t(j + i) * ld + c] = Bs[i * kTrsmThreads + threadIdx.x];
 }
 
+// Same solve for a fixed triangle size CNT: the thread's column lives in registers and the
+// substitution is written column by column (b_t final, then every row below it updated), so
+// the CNT - t - 1 updates of a step are independent and no shared-memory traffic touches the
+// right-hand side; only the triangle (unit lower part) is staged in shared memory.
+template <typename T2, int CNT>
+__global__ void __launch_bounds__(kTrsmThreads) trsm_reg_kernel(T2* G, int64_t sG, int ld, int j, int c0, int c1) {
+    using R = typename Real<T2>::R;
+    __shared__ T2 Ls[CNT][CNT];
+    const int f = blockIdx.y;
+    T2* A = G + f * sG;
+    for (int idx = threadIdx.x; idx < CNT * CNT; idx += blockDim.x) {
+        const int r = idx / CNT, cc = idx - r * CNT;
+        Ls[r][cc] = cc < r ? A[int64_t(j + r) * ld + j + cc] : mk<T2>(R(0), R(0));
+    }
+    __syncthreads();
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= c1) return;
+    T2 b[CNT];
+#pragma unroll
+    for (int i = 0; i < CNT; ++i) b[i] = A[int64_t(j + i) * ld + c];
+#pragma unroll
+    for (int t = 0; t + 1 < CNT; ++t)
+#pragma unroll
+        for (int i = t + 1; i < CNT; ++i) cfms(b[i], Ls[i][t], b[t]);
+#pragma unroll
+    for (int i = 1; i < CNT; ++i) A[int64_t(j + i) * ld + c] = b[i];
+}
+
 // ----------------------------------------------------------------- gemm update
 // C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] * B[k0:k0+K, c0:c1] within one matrix of the batch
 // (FP64; the FP32 update is the register-tiled kernel of cgemm_f32.cu).
@@ -465,6 +493,16 @@ void launch_trsm(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int j, int c
     }
     dim3 grid(ceil_div(c1 - c0, kTrsmThreads), F);
     ProfScope ps(PK_TRSM, 8.0 * F * double(cnt) * cnt / 2.0 * (c1 - c0), st);
+    if (cnt == 16) {
+        trsm_reg_kernel<T2, 16><<<grid, kTrsmThreads, 0, st>>>(G, sG, ld, j, c0, c1);
+        return;
+    }
+    if constexpr (sizeof(R) == 4) {
+        if (cnt == 32) {
+            trsm_reg_kernel<T2, 32><<<grid, kTrsmThreads, 0, st>>>(G, sG, ld, j, c0, c1);
+            return;
+        }
+    }
     trsm_kernel<T2><<<grid, kTrsmThreads, smem, st>>>(G, sG, ld, j, cnt, c0, c1);
 }
 
