@@ -201,7 +201,7 @@ def run_rom(args):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     wr = api.rom_windows(model, F, rcv, grid, q=args.rom_q, kmax=args.rom_kmax, max_shifts=12, tol=args.rom_tol,
-                         max_windows=args.rom_windows, min_points=8)
+                         max_windows=args.rom_windows, min_points=8, reuse=not args.rom_no_reuse)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -229,8 +229,10 @@ def run_rom(args):
     print(json.dumps({
         "mode": "rom", "metric": "ROM sweep frequencies/s (config 4 band, windowed)", "value": len(grid) / t_sweep,
         "unit": UNIT, "band_hz": [float(grid[0]), float(grid[-1])], "frequencies": int(len(grid)),
-        "windows": [{"lo": float(a), "hi": float(b), "k": int(k), "points": int(n), "maxest": float(m)}
-                    for a, b, k, n, m in zip(wr.lo, wr.hi, wr.k, wr.nshift, wr.maxest)],
+        "windows": [{"lo": float(a), "hi": float(b), "k": int(k), "points": int(n), "reused_points": int(r),
+                     "maxest": float(m)}
+                    for a, b, k, n, r, m in zip(wr.lo, wr.hi, wr.k, wr.nshift, wr.nreused, wr.maxest)],
+        "cross_window_reuse": not args.rom_no_reuse,
         "build_s": t_build, "sweep_ms": t_sweep * 1e3,
         "e2e": {"value": len(grid) / (t_build + t_sweep), "unit": UNIT, "note": "window build + one sweep"},
         "check": {"frequencies": int(len(chk)), "max_spl_err_db": float(db.max()),
@@ -394,6 +396,8 @@ def main():
     ap.add_argument("--rom-kmax", type=int, default=400)
     ap.add_argument("--rom-tol", type=float, default=1e-4)
     ap.add_argument("--rom-windows", type=int, default=16)
+    ap.add_argument("--rom-no-reuse", action="store_true",
+                    help="windows start from fresh points instead of their enclosing windows' points")
     ap.add_argument("--design-shifts", type=int, default=16)
     ap.add_argument("--mode", default="sweep", choices=["sweep", "lu_window", "rom", "design", "kernels"],
                     help="lu_window: only the batched band-LU of config-2-sized windows (for kernel profiling)")

@@ -347,21 +347,29 @@ typedef struct {
     fsi_greedy_opts greedy;       /* per window                                     */
     int max_windows;
     int min_points;               /* a window is not split below this many points  */
+    int reuse;                    /* 1: a window split from a larger one starts from
+                                     the larger windows' expansion points in its band,
+                                     their Krylov blocks copied from a moment store
+                                     (no new factorisation); 0: fresh points at the
+                                     window's quarter midpoints                      */
 } fsi_window_opts;
 
-/* Workspace bytes for rom_windows (one greedy workspace + an n x kmax basis). */
+/* Workspace bytes for rom_windows (one greedy workspace + an n x kmax basis, and with
+ * reuse a moment store of 4 * max_shifts * q * nrhs columns of n). */
 fsi_status rom_windows_workspace(const fsi_dims* dims, int nrhs, const fsi_window_opts* opts, size_t* bytes);
 
 /* Windows in increasing frequency order.  Device outputs, slot w of each:
  * KR/DR/MR at w*kmax*kmax (k_w x k_w, ld k_w), fR at w*kmax*nrhs (k_w x nrhs),
  * CR at w*nrcv*kmax (nrcv x k_w); buffers hold max_windows slots.  Host
  * outputs (max_windows entries): window [lo, hi] (first and last candidate),
- * k, number of expansion points, largest final estimate.  Errors as rom_greedy. */
+ * k, number of expansion points, largest final estimate, and (nullable) how many
+ * of the points were reused from enclosing windows.  Errors as rom_greedy. */
 fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64* F, int nrhs,
                        const double* cand_hz, int ncand, const fsi_window_opts* opts, void* ws,
                        size_t ws_bytes, const int32_t* rcv, int nrcv, fsi_c64* KR, fsi_c64* DR,
                        fsi_c64* MR, fsi_c64* fR, fsi_c64* CR, int* nwin_out, double* lo_out,
-                       double* hi_out, int* k_out, int* nshift_out, double* maxest_out, void* stream);
+                       double* hi_out, int* k_out, int* nshift_out, double* maxest_out,
+                       int* nreused_out, void* stream);
 
 /* Workspace bytes for rom_windows_sweep. */
 fsi_status rom_windows_sweep_workspace(int kmax, int nrhs, int batch, size_t* bytes);

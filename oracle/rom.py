@@ -225,32 +225,44 @@ def greedy(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts:
 
 
 def windows(asm, F, rcv_dofs, cand_hz, q: int, kmax: int, tol: float, max_shifts: int,
-            max_windows: int, min_points: int):
+            max_windows: int, min_points: int, reuse: bool = True):
     """Local ROMs over frequency windows (Sec. 3.3: one fROM per window).
 
-    The candidate band starts as one window; each window gets its own greedy
-    ROM started from the candidates nearest its quarter midpoints.  A window
-    whose greedy ends with its largest estimate above tol is bisected by
-    candidate count (left half first), down to min_points candidates and at
-    most max_windows windows in all.
+    The candidate band starts as one window.  A window whose greedy ends with its
+    largest estimate above tol is bisected by candidate count (left half first), down
+    to min_points candidates and at most max_windows windows in all.  Each window's
+    greedy starts from the expansion points of the windows it was split from that lie
+    in its band (in the order they were chosen; with reuse), else from the candidates
+    nearest its quarter midpoints.
     """
     cand_hz = np.asarray(cand_hz, dtype=float)
     todo = [(0, len(cand_hz))]
     out = []
+    split = []   # (i0, i1, shifts) of the windows that were bisected, outermost first
     while todo:
         i0, i1 = todo.pop(0)
         c = cand_hz[i0:i1]
+        split = [a for a in split if a[0] <= i0 and i1 <= a[1]]
         init = []
-        for qq in range(4):
-            t = c[0] + (c[-1] - c[0]) * (qq + 0.5) / 4.0
-            pick = float(c[int(np.argmin(np.abs(c - t)))])
-            if pick not in init and len(init) < max_shifts:
-                init.append(pick)
+        if reuse:
+            for a in split:
+                for sh in a[2]:
+                    if c[0] <= sh <= c[-1] and sh not in init:
+                        init.append(sh)
+            init = init[:max_shifts]
+        nreused = len(init)
+        if not init:
+            for qq in range(4):
+                t = c[0] + (c[-1] - c[0]) * (qq + 0.5) / 4.0
+                pick = float(c[int(np.argmin(np.abs(c - t)))])
+                if pick not in init and len(init) < max_shifts:
+                    init.append(pick)
         shifts, V, rm, hist = greedy(asm, F, rcv_dofs, c, q, kmax, tol, max_shifts, initial_hz=init)
         mx = hist[-1]
         if mx > tol and (i1 - i0) >= 2 * max(1, min_points) and len(out) + len(todo) + 2 <= max_windows:
             mid = i0 + (i1 - i0) // 2
             todo[0:0] = [(i0, mid), (mid, i1)]
+            split.append((i0, i1, shifts))
             continue
-        out.append(dict(lo=float(c[0]), hi=float(c[-1]), shifts=shifts, V=V, rm=rm, maxest=mx))
+        out.append(dict(lo=float(c[0]), hi=float(c[-1]), shifts=shifts, V=V, rm=rm, maxest=mx, reused=nreused))
     return out

@@ -61,7 +61,7 @@ class fsi_greedy_opts(C.Structure):
 
 
 class fsi_window_opts(C.Structure):
-    _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int)]
+    _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int), ("reuse", c_int)]
 
 
 class fsi_rom_item(C.Structure):
@@ -115,7 +115,7 @@ SIGNATURES = {
     "rom_windows": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_double_p, c_int,
                             C.POINTER(fsi_window_opts), c_void_p, c_size_t, c_void_p, c_int, c_void_p, c_void_p,
                             c_void_p, c_void_p, c_void_p, C.POINTER(c_int), c_double_p, c_double_p, c_int32_p,
-                            c_int32_p, c_double_p, c_void_p]),
+                            c_int32_p, c_double_p, c_int32_p, c_void_p]),
     "rom_windows_sweep_workspace": (c_int, [c_int, c_int, c_int, C.POINTER(c_size_t)]),
     "rom_windows_sweep": (c_int, [c_int, c_double_p, c_double_p, c_int32_p, c_int, c_void_p, c_void_p, c_void_p,
                                   c_void_p, c_void_p, c_int, c_int, c_double_p, c_int, c_int, c_void_p, c_size_t,

@@ -411,6 +411,7 @@ class WindowedROM:
     k: np.ndarray         # basis columns per window
     nshift: np.ndarray    # expansion points per window
     maxest: np.ndarray    # largest final residual estimate per window
+    nreused: np.ndarray   # expansion points reused from enclosing windows (no new factorisation)
     kmax: int
     nrhs: int
     nrcv: int
@@ -419,8 +420,9 @@ class WindowedROM:
 
 def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
                 max_windows: int = 16, min_points: int = 4, precision="fp32_ir", max_refine=10,
-                refine_tol=1e-10, second_order=-1) -> WindowedROM:
-    """Local ROMs over windows of the candidate band (C-ABI rom_windows)."""
+                refine_tol=1e-10, second_order=-1, reuse: bool = True) -> WindowedROM:
+    """Local ROMs over windows of the candidate band (C-ABI rom_windows); with reuse, a window
+    split from a larger one starts from that window's expansion points in its band."""
     torch = _torch()
     lib = L.load()
     cand = np.ascontiguousarray(np.asarray(cand_hz, dtype=np.float64))
@@ -428,7 +430,7 @@ def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shif
     o = L.fsi_window_opts()
     o.greedy.q, o.greedy.kmax, o.greedy.max_shifts, o.greedy.tol = int(q), int(kmax), int(max_shifts), float(tol)
     o.greedy.build = _rom_opts(precision, max_refine, refine_tol, second_order)
-    o.max_windows, o.min_points = int(max_windows), int(min_points)
+    o.max_windows, o.min_points, o.reuse = int(max_windows), int(min_points), int(bool(reuse))
     need = C.c_size_t()
     L.check(lib.rom_windows_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_windows_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
@@ -443,17 +445,19 @@ def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shif
     CR = torch.empty(W * nrcv * kmax, dtype=torch.complex128, device="cuda")
     nw = C.c_int(0)
     lo, hi, mx = np.zeros(W), np.zeros(W), np.zeros(W)
-    kk, ns = np.zeros(W, np.int32), np.zeros(W, np.int32)
+    kk, ns, nr = np.zeros(W, np.int32), np.zeros(W, np.int32), np.zeros(W, np.int32)
     L.check(lib.rom_windows(C.byref(model.dims), _ptr(model.buf), _ptr(Fc), nrhs, cand.ctypes.data_as(L.c_double_p),
                             int(cand.size), C.byref(o), _ptr(ws), C.c_size_t(need.value), _ptr(r), nrcv, _ptr(KR),
                             _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR), C.byref(nw), lo.ctypes.data_as(L.c_double_p),
                             hi.ctypes.data_as(L.c_double_p), kk.ctypes.data_as(L.c_int32_p),
-                            ns.ctypes.data_as(L.c_int32_p), mx.ctypes.data_as(L.c_double_p), _stream_ptr()),
+                            ns.ctypes.data_as(L.c_int32_p), mx.ctypes.data_as(L.c_double_p),
+                            nr.ctypes.data_as(L.c_int32_p), _stream_ptr()),
             "rom_windows")
     n = nw.value
     del ws
     return WindowedROM(lo=lo[:n].copy(), hi=hi[:n].copy(), k=kk[:n].copy(), nshift=ns[:n].copy(),
-                       maxest=mx[:n].copy(), kmax=int(kmax), nrhs=nrhs, nrcv=nrcv, bufs=(KR, DR, MR, fR, CR))
+                       maxest=mx[:n].copy(), nreused=nr[:n].copy(), kmax=int(kmax), nrhs=nrhs, nrcv=nrcv,
+                       bufs=(KR, DR, MR, fR, CR))
 
 
 def rom_windows_sweep(wr: WindowedROM, freqs_hz, batch: int = 256):

@@ -482,6 +482,7 @@ struct RomWS {
     double *norms, *fnorms, *absn;
     CgsBufs cg;
     double2 *Qs, *Ps;
+    double2* Ql;   // local Krylov block of one expansion point (first order), n x q*nrhs
     int64_t sV;
 
     void carve(Carver& c, const fsi_dims& d, int nrhs, int q, int kmax) {
@@ -503,6 +504,7 @@ struct RomWS {
         cg.scal = c.take<double>(2);
         Qs = c.take<double2>(size_t(d.n) * q);
         Ps = c.take<double2>(size_t(d.n) * q);
+        Ql = c.take<double2>(size_t(d.n) * q * nrhs);
     }
 };
 
@@ -531,7 +533,7 @@ fsi_status shifted_solve(const DevModel& m, RomWS<R>& w, double om, const double
 template <typename R>
 fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* shifts, int nshift, int q,
                          const double2* F, int nrhs, int kmax, const fsi_rom_opts& o, void* ws, size_t ws_bytes,
-                         double2* V, int k_in, int* k_out, cudaStream_t st) {
+                         double2* V, int k_in, int* k_out, cudaStream_t st, MomentStore* store) {
     Carver c(ws, ws_bytes);
     RomWS<R> w;
     w.carve(c, d, nrhs, q, kmax);
@@ -572,27 +574,44 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
             set_error("singular shifted matrix at an expansion point");
             return FSI_ESINGULAR;
         }
+        // room in the store for this point's block (else the local block stays in the workspace)
+        const int64_t blk_cols = int64_t(q) * nrhs;
+        const bool keep = store && store->used + blk_cols <= store->cap;
+        const int64_t col0 = keep ? store->used : 0;
+        int nkept = 0;
         if (!second) {
-            // Eq. 10: block of moments, v_0 = Kt^-1 F, v_m = Kt^-1 M q_{m-1} (q: accepted new columns)
+            // Eq. 10: local Arnoldi on Kt^-1 M started from Kt^-1 F (the point's own Krylov space,
+            // orthonormalised within the point); each accepted local vector is then CGS2-appended to V
+            double2* Ql = keep ? store->buf + col0 * n : w.Ql;
+            int kl = 0;
+            const int klmax = q * nrhs;
             ROM_CUDA(cudaMemcpyAsync(w.B, F, sizeof(double2) * n * nrhs, cudaMemcpyDeviceToDevice, st));
             int nr = nrhs;
             for (int mom = 0; mom < q && nr > 0 && k < kmax; ++mom) {
                 s = shifted_solve<R>(m, w, om, w.B, nr, max_it, tol, 1.0, w.X, st);
                 if (s != FSI_OK) return s;
-                const int k0 = k;
-                for (int cc = 0; cc < nr && k < kmax; ++cc) {
+                const int kl0 = kl;
+                for (int cc = 0; cc < nr; ++cc) {
                     bool acc = false;
-                    s = cgs2_append(V, n, k, kmax, w.X + int64_t(cc) * n, w.cg, acc, st);
+                    s = cgs2_append(Ql, n, kl, klmax, w.X + int64_t(cc) * n, w.cg, acc, st);
                     if (s != FSI_OK) return s;
                 }
-                nr = k - k0;
+                for (int j = kl0; j < kl && k < kmax; ++j) {
+                    ROM_CUDA(cudaMemcpyAsync(w.W, Ql + int64_t(j) * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice,
+                                             st));
+                    bool acc = false;
+                    s = cgs2_append(V, n, k, kmax, w.W, w.cg, acc, st);
+                    if (s != FSI_OK) return s;
+                }
+                nr = kl - kl0;
                 if (nr > 0 && mom + 1 < q) {
                     spmv_kernel<<<dim3(spmv_grid_x(n, nr), nr), kRowThreads, 0, st>>>(
-                        m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), V + int64_t(k0) * n, w.B, nr,
+                        m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), Ql + int64_t(kl0) * n, w.B, nr,
                         false);
                     ROM_LAUNCH();
                 }
             }
+            nkept = kl;
         } else {
             // Eq. 9 by SOAR per load column: q_0 = u/|u|, u = -Kt^-1 f; r = A q_j + B p_j
             const double2 dt = make_double2(0.0, 2.0 * om);   // Dt = D + 2 i w_j M
@@ -639,6 +658,11 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                     ROM_LAUNCH();
                     ++nq;
                 }
+                if (keep) {
+                    ROM_CUDA(cudaMemcpyAsync(store->buf + (col0 + nkept) * n, w.Qs, sizeof(double2) * n * nq,
+                                             cudaMemcpyDeviceToDevice, st));
+                    nkept += nq;
+                }
                 for (int j = 0; j < nq && k < kmax; ++j) {
                     ROM_CUDA(cudaMemcpyAsync(w.W, w.Qs + int64_t(j) * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice,
                                              st));
@@ -647,6 +671,11 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                     if (s != FSI_OK) return s;
                 }
             }
+        }
+        // a block cut short by the column budget is not the point's whole Krylov space: not kept
+        if (keep && nkept > 0 && k < kmax) {
+            store->blocks.push_back(MomentBlock{shifts[sidx], col0, nkept, store->lo, store->hi});
+            store->used = col0 + nkept;
         }
     }
     ROM_CUDA(cudaStreamSynchronize(st));
@@ -664,18 +693,48 @@ size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax) {
 template <typename R>
 fsi_status rom_build_append(const fsi_dims& d, const void* d_model, const double* shifts, int nshift, int q,
                             const double2* F, int nrhs, int kmax, const fsi_rom_opts& o, void* ws, size_t ws_bytes,
-                            double2* V, int k_in, int* k_out, cudaStream_t st) {
-    return run_rom_build<R>(d, d_model, shifts, nshift, q, F, nrhs, kmax, o, ws, ws_bytes, V, k_in, k_out, st);
+                            double2* V, int k_in, int* k_out, cudaStream_t st, MomentStore* store) {
+    return run_rom_build<R>(d, d_model, shifts, nshift, q, F, nrhs, kmax, o, ws, ws_bytes, V, k_in, k_out, st, store);
+}
+
+size_t rom_append_ws(int64_t n, int kmax) {
+    Carver c(nullptr, 0);
+    c.take<double2>(size_t(kChunks) * (kmax + 1));
+    c.take<double2>(size_t(kmax) + 1);
+    c.take<double>(2);
+    c.take<double2>(size_t(n));
+    return align_up(c.used);
+}
+
+fsi_status rom_append_columns(double2* V, int64_t n, int& k, int kmax, const double2* cols, int ncol, void* ws,
+                              size_t ws_bytes, cudaStream_t st) {
+    Carver c(ws, ws_bytes);
+    CgsBufs b;
+    b.partial = c.take<double2>(size_t(kChunks) * (kmax + 1));
+    b.H = c.take<double2>(size_t(kmax) + 1);
+    b.scal = c.take<double>(2);
+    double2* tmp = c.take<double2>(size_t(n));
+    if (!c.fits()) {
+        set_error("column append workspace too small");
+        return FSI_ENOMEM;
+    }
+    for (int j = 0; j < ncol && k < kmax; ++j) {
+        ROM_CUDA(cudaMemcpyAsync(tmp, cols + int64_t(j) * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice, st));
+        bool acc = false;
+        fsi_status s = cgs2_append(V, n, k, kmax, tmp, b, acc, st);
+        if (s != FSI_OK) return s;
+    }
+    return FSI_OK;
 }
 
 template size_t rom_build_ws<float>(const fsi_dims&, int, int, int);
 template size_t rom_build_ws<double>(const fsi_dims&, int, int, int);
 template fsi_status rom_build_append<float>(const fsi_dims&, const void*, const double*, int, int, const double2*, int,
                                             int, const fsi_rom_opts&, void*, size_t, double2*, int, int*,
-                                            cudaStream_t);
+                                            cudaStream_t, MomentStore*);
 template fsi_status rom_build_append<double>(const fsi_dims&, const void*, const double*, int, int, const double2*,
                                              int, int, const fsi_rom_opts&, void*, size_t, double2*, int, int*,
-                                             cudaStream_t);
+                                             cudaStream_t, MomentStore*);
 
 fsi_status reduced_receivers(const ReducedBatch& rb, const double2* CR, int nrcv, double2* p, double* spl,
                              cudaStream_t st) {
@@ -760,9 +819,9 @@ fsi_status rom_build(const fsi_dims* dims, const void* d_model, const double* sh
     double2* Vd = reinterpret_cast<double2*>(V);
     if (opts->precision == FSI_FP64)
         return run_rom_build<double>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd, 0,
-                                     k_out, st);
+                                     k_out, st, nullptr);
     return run_rom_build<float>(*dims, d_model, shifts_hz, nshift, q, Fd, nrhs, kmax, *opts, ws, ws_bytes, Vd, 0,
-                                k_out, st);
+                                k_out, st, nullptr);
 }
 
 fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k, const fsi_c64* F, int nrhs,

@@ -333,7 +333,8 @@ fsi_status run_greedy(const fsi_dims& d, const void* d_model, const double2* F, 
                       int ncand, const double* init_hz, int ninit, const fsi_greedy_opts& o, void* ws, size_t ws_bytes,
                       double2* V, int* k_out, double2* KR, double2* DR, double2* MR, double2* fR, const int32_t* rcv,
                       int nrcv, double2* CR, double* shifts_out, int* nshift_out, double* est_out, double* hist_out,
-                      cudaStream_t st) {
+                      cudaStream_t st, int k_seed = 0, const double* seed_hz = nullptr, int nseed = 0,
+                      MomentStore* store = nullptr) {
     Carver c(ws, ws_bytes);
     GreedyWS w;
     w.carve<R>(c, d, nrhs, o);
@@ -365,16 +366,21 @@ fsi_status run_greedy(const fsi_dims& d, const void* d_model, const double2* F, 
         return mn;
     }()
                                   : 0.0;
-    std::vector<double> shifts;
+    // expansion points whose moments V already holds (k_seed columns), then the fresh initial points
+    std::vector<double> shifts(seed_hz, seed_hz + nseed), fresh;
     if (ninit > 0)
-        shifts.assign(init_hz, init_hz + ninit);
-    else
-        shifts.push_back(cand[ncand / 2]);
-    if (int(shifts.size()) > o.max_shifts) shifts.resize(o.max_shifts);
-    int k = 0, k1 = 0;
-    fsi_status s = rom_build_append<R>(d, d_model, shifts.data(), int(shifts.size()), o.q, F, nrhs, o.kmax, o.build,
-                                       w.build, w.build_bytes, V, 0, &k1, st);
-    if (s != FSI_OK) return s;
+        fresh.assign(init_hz, init_hz + ninit);
+    else if (nseed == 0)
+        fresh.push_back(cand[ncand / 2]);
+    if (int(shifts.size() + fresh.size()) > o.max_shifts) fresh.resize(std::max(0, o.max_shifts - nseed));
+    int k = k_seed, k1 = k_seed;
+    fsi_status s = FSI_OK;
+    if (!fresh.empty()) {
+        s = rom_build_append<R>(d, d_model, fresh.data(), int(fresh.size()), o.q, F, nrhs, o.kmax, o.build, w.build,
+                                w.build_bytes, V, k_seed, &k1, st, store);
+        if (s != FSI_OK) return s;
+        shifts.insert(shifts.end(), fresh.begin(), fresh.end());
+    }
     s = grow_gram(m, w, V, F, nrhs, 0, k1, st);
     if (s != FSI_OK) return s;
     k = k1;
@@ -443,7 +449,7 @@ fsi_status run_greedy(const fsi_dims& d, const void* d_model, const double2* F, 
         double nxt = cand[inext];
         shifts.push_back(nxt);
         s = rom_build_append<R>(d, d_model, &nxt, 1, o.q, F, nrhs, o.kmax, o.build, w.build, w.build_bytes, V, k, &k1,
-                                st);
+                                st, store);
         if (s != FSI_OK) return s;
         s = grow_gram(m, w, V, F, nrhs, k, k1, st);
         if (s != FSI_OK) return s;
@@ -494,22 +500,38 @@ __global__ void output_error_kernel(const double2* pref, const double2* p, int n
 
 struct WindowResult {
     double lo, hi, maxest;
-    int k, nshift;
+    int k, nshift, nreused;
 };
+
+// columns of the moment store of one rom_windows call: the Krylov blocks of up to four
+// nested windows' expansion points (deeper ancestors' points are recomputed when needed)
+inline int64_t store_cols(const fsi_greedy_opts& g, int nrhs) { return int64_t(4) * g.max_shifts * g.q * nrhs; }
 
 // l-fROM windows: greedy ROM per window of candidates; a window whose greedy stops above tol
 // (point or column budget spent) is bisected, down to min_points candidates, at most
 // max_windows windows in all.  Window w's reduced matrices go to slot w of the outputs.
+// Cross-window reuse (o.reuse): a window starts from the expansion points of the windows it
+// was split from that lie in its band, instead of fresh quarter-midpoint points; their
+// Krylov blocks are copied from the moment store (no factorisation or moment solve) and
+// CGS2-appended, and only points whose blocks were not kept are recomputed.  Windows are
+// processed depth first, so the store holds the blocks of the current window's ancestors
+// (and of its finished siblings' subtrees, dropped before the next window starts).
 template <typename R>
 fsi_status run_windows(const fsi_dims& d, const void* d_model, const double2* F, int nrhs, const double* cand,
                        int ncand, const fsi_window_opts& o, void* ws, size_t ws_bytes, double2* V, const int32_t* rcv,
                        int nrcv, double2* KR, double2* DR, double2* MR, double2* fR, double2* CR,
-                       std::vector<WindowResult>& out, cudaStream_t st) {
+                       MomentStore* store, void* aws, size_t aws_bytes, std::vector<WindowResult>& out,
+                       cudaStream_t st) {
     const int K = o.greedy.kmax;
     struct Range {
         int i0, i1;
     };
+    struct Ancestor {
+        int i0, i1;
+        std::vector<double> shifts;
+    };
     std::vector<Range> todo{{0, ncand}};
+    std::vector<Ancestor> anc;   // bisected windows, outermost first
     std::vector<double> shifts(o.greedy.max_shifts), hist(o.greedy.max_shifts), est(ncand);
     out.clear();
     while (!todo.empty()) {
@@ -517,21 +539,54 @@ fsi_status run_windows(const fsi_dims& d, const void* d_model, const double2* F,
         todo.erase(todo.begin());
         const int nc = r.i1 - r.i0;
         const double* c = cand + r.i0;
-        // initial points: the candidates nearest the window's quarter midpoints
-        std::vector<double> init;
-        for (int qq = 0; qq < 4 && int(init.size()) < o.greedy.max_shifts; ++qq) {
-            const double t = c[0] + (c[nc - 1] - c[0]) * (qq + 0.5) / 4.0;
-            int best = 0;
-            for (int i = 1; i < nc; ++i)
-                if (std::fabs(c[i] - t) < std::fabs(c[best] - t)) best = i;
-            if (std::find(init.begin(), init.end(), c[best]) == init.end()) init.push_back(c[best]);
+        auto contains = [&](int lo, int hi) { return lo <= r.i0 && r.i1 <= hi; };
+        while (!anc.empty() && !contains(anc.back().i0, anc.back().i1)) anc.pop_back();
+        std::vector<double> seed, init;
+        int k = 0;
+        if (o.reuse && store) {
+            // finished subtrees' blocks sit on top of the store: drop them
+            while (!store->blocks.empty() && !contains(store->blocks.back().lo, store->blocks.back().hi))
+                store->blocks.pop_back();
+            store->used = store->blocks.empty() ? 0 : store->blocks.back().col0 + store->blocks.back().ncol;
+            store->lo = r.i0;
+            store->hi = r.i1;
+            std::vector<double> inband;   // ancestors' points in this band, first occurrence order
+            for (const Ancestor& a : anc)
+                for (double sh : a.shifts)
+                    if (sh >= c[0] && sh <= c[nc - 1] && std::find(inband.begin(), inband.end(), sh) == inband.end())
+                        inband.push_back(sh);
+            if (int(inband.size()) > o.greedy.max_shifts) inband.resize(o.greedy.max_shifts);
+            for (double sh : inband) {
+                const MomentBlock* blk = nullptr;
+                for (const MomentBlock& b : store->blocks)
+                    if (b.shift == sh) blk = &b;
+                if (blk) {
+                    fsi_status s = rom_append_columns(V, d.n, k, K, store->buf + blk->col0 * d.n, blk->ncol, aws,
+                                                      aws_bytes, st);
+                    if (s != FSI_OK) return s;
+                    seed.push_back(sh);
+                } else {
+                    init.push_back(sh);
+                }
+            }
+        }
+        if (seed.empty() && init.empty()) {
+            // initial points: the candidates nearest the window's quarter midpoints
+            for (int qq = 0; qq < 4 && int(init.size()) < o.greedy.max_shifts; ++qq) {
+                const double t = c[0] + (c[nc - 1] - c[0]) * (qq + 0.5) / 4.0;
+                int best = 0;
+                for (int i = 1; i < nc; ++i)
+                    if (std::fabs(c[i] - t) < std::fabs(c[best] - t)) best = i;
+                if (std::find(init.begin(), init.end(), c[best]) == init.end()) init.push_back(c[best]);
+            }
         }
         const size_t slot = out.size();
-        int k = 0, nsh = 0;
+        int kw = 0, nsh = 0;
         fsi_status s = run_greedy<R>(d, d_model, F, nrhs, c, nc, init.data(), int(init.size()), o.greedy, ws, ws_bytes,
-                                     V, &k, KR + slot * K * K, DR + slot * K * K, MR + slot * K * K,
+                                     V, &kw, KR + slot * K * K, DR + slot * K * K, MR + slot * K * K,
                                      fR + slot * K * nrhs, rcv, nrcv, CR ? CR + slot * nrcv * K : nullptr,
-                                     shifts.data(), &nsh, est.data(), hist.data(), st);
+                                     shifts.data(), &nsh, est.data(), hist.data(), st, k, seed.data(),
+                                     int(seed.size()), o.reuse ? store : nullptr);
         if (s != FSI_OK) return s;
         const double mx = *std::max_element(est.begin(), est.begin() + nc);
         const bool can_split = nc >= 2 * std::max(1, o.min_points) &&
@@ -540,9 +595,10 @@ fsi_status run_windows(const fsi_dims& d, const void* d_model, const double2* F,
             const int mid = r.i0 + nc / 2;
             todo.insert(todo.begin(), Range{mid, r.i1});
             todo.insert(todo.begin(), Range{r.i0, mid});
+            anc.push_back(Ancestor{r.i0, r.i1, std::vector<double>(shifts.begin(), shifts.begin() + nsh)});
             continue;
         }
-        out.push_back(WindowResult{c[0], c[nc - 1], mx, k, nsh});
+        out.push_back(WindowResult{c[0], c[nc - 1], mx, kw, nsh, int(seed.size())});
     }
     return FSI_OK;
 }
@@ -603,6 +659,10 @@ fsi_status rom_windows_workspace(const fsi_dims* dims, int nrhs, const fsi_windo
     Carver c(nullptr, 0);
     c.take<char>(greedy_ws_bytes(*dims, nrhs, o->greedy));
     c.take<double2>(size_t(dims->n) * o->greedy.kmax);   // basis scratch
+    if (o->reuse) {
+        c.take<char>(rom_append_ws(dims->n, o->greedy.kmax));
+        c.take<double2>(size_t(dims->n) * store_cols(o->greedy, nrhs));
+    }
     *bytes = align_up(c.used);
     return FSI_OK;
 }
@@ -611,7 +671,7 @@ fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64*
                        int ncand, const fsi_window_opts* o, void* ws, size_t ws_bytes, const int32_t* rcv, int nrcv,
                        fsi_c64* KR, fsi_c64* DR, fsi_c64* MR, fsi_c64* fR, fsi_c64* CR, int* nwin_out,
                        double* lo_out, double* hi_out, int* k_out, int* nshift_out, double* maxest_out,
-                       void* stream) {
+                       int* nreused_out, void* stream) {
     if (!(dims && d_model && F && cand_hz && o && ws && rcv && KR && DR && MR && fR && CR && nwin_out && lo_out &&
           hi_out && k_out && nshift_out && maxest_out)) {
         set_error("rom_windows: NULL argument");
@@ -636,6 +696,15 @@ fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64*
     const size_t gbytes = greedy_ws_bytes(*dims, nrhs, g);
     void* gws = c.take<char>(gbytes);
     double2* V = c.take<double2>(size_t(dims->n) * g.kmax);
+    MomentStore store;
+    void* aws = nullptr;
+    size_t abytes = 0;
+    if (o->reuse) {
+        abytes = rom_append_ws(dims->n, g.kmax);
+        aws = c.take<char>(abytes);
+        store.cap = store_cols(g, nrhs);
+        store.buf = c.take<double2>(size_t(dims->n) * store.cap);
+    }
     if (!c.fits()) {
         set_error("rom_windows workspace too small: need " + std::to_string(align_up(c.used)) + " bytes");
         return FSI_ENOMEM;
@@ -644,12 +713,13 @@ fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64*
     auto m2 = [](fsi_c64* p) { return reinterpret_cast<double2*>(p); };
     std::vector<WindowResult> out;
     const double2* Fd = reinterpret_cast<const double2*>(F);
+    MomentStore* sp = o->reuse ? &store : nullptr;
     fsi_status s =
         g.build.precision == FSI_FP64
             ? run_windows<double>(*dims, d_model, Fd, nrhs, cand_hz, ncand, *o, gws, gbytes, V, rcv, nrcv, m2(KR),
-                                  m2(DR), m2(MR), m2(fR), m2(CR), out, st)
+                                  m2(DR), m2(MR), m2(fR), m2(CR), sp, aws, abytes, out, st)
             : run_windows<float>(*dims, d_model, Fd, nrhs, cand_hz, ncand, *o, gws, gbytes, V, rcv, nrcv, m2(KR),
-                                 m2(DR), m2(MR), m2(fR), m2(CR), out, st);
+                                 m2(DR), m2(MR), m2(fR), m2(CR), sp, aws, abytes, out, st);
     if (s != FSI_OK) return s;
     *nwin_out = int(out.size());
     for (size_t w = 0; w < out.size(); ++w) {
@@ -658,6 +728,7 @@ fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64*
         k_out[w] = out[w].k;
         nshift_out[w] = out[w].nshift;
         maxest_out[w] = out[w].maxest;
+        if (nreused_out) nreused_out[w] = out[w].nreused;
     }
     return FSI_OK;
 }

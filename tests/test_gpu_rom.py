@@ -136,9 +136,11 @@ def test_greedy_matches_oracle_greedy(floor):
     assert rom.relative_error(y, ps.cpu().numpy()).max() < 1e-5
 
 
-def test_windows_match_oracle_windows():
+@pytest.mark.parametrize("reuse", [False, True])
+def test_windows_match_oracle_windows(reuse):
     """Local ROM windows on the GPU against the oracle's windows: same partition, same
-    points per window, same final estimates, same reduced outputs per window."""
+    points per window (and as many reused from enclosing windows), same final estimates,
+    same reduced outputs per window."""
     torch = need_cuda()
     from paper_2310_04734_gb300 import api
     w = W.small_model(floor=False)
@@ -148,15 +150,18 @@ def test_windows_match_oracle_windows():
     rcv = torch.tensor(api.receiver_dofs(spec, w.receivers), device="cuda")
     cand = np.arange(40.0, 300.0, 10.0)
     g = api.rom_windows(model, F, rcv, cand, q=2, kmax=60, max_shifts=4, tol=1e-6, max_windows=4, min_points=3,
-                        precision="fp64", max_refine=5, refine_tol=1e-13)
+                        precision="fp64", max_refine=5, refine_tol=1e-13, reuse=reuse)
     asm = fem.assemble(spec)
     Fo = fem.load_matrix(spec, w.loads, w.n_rhs)
     rco = fem.receiver_dofs(spec, w.receivers)
-    wins = rom.windows(asm, Fo, rco, cand, q=2, kmax=60, tol=1e-6, max_shifts=4, max_windows=4, min_points=3)
+    wins = rom.windows(asm, Fo, rco, cand, q=2, kmax=60, tol=1e-6, max_shifts=4, max_windows=4, min_points=3,
+                       reuse=reuse)
     print("windows gpu", g.lo.tolist(), g.hi.tolist(), g.maxest.tolist(), "oracle",
           [(x["lo"], x["hi"], x["maxest"]) for x in wins])
     assert g.lo.tolist() == [x["lo"] for x in wins] and g.hi.tolist() == [x["hi"] for x in wins]
     assert g.nshift.tolist() == [len(x["shifts"]) for x in wins]
+    assert g.nreused.tolist() == [x["reused"] for x in wins]
+    assert (g.nreused.sum() > 0) == reuse
     # estimates near the rounding level of a solve (windows whose every candidate is an
     # expansion point) carry no digits; compare the others
     mo = np.array([x["maxest"] for x in wins])

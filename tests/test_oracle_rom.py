@@ -199,3 +199,28 @@ def test_full_residual_vanishes_at_expansion_points_and_with_a_complete_basis():
     Q, _ = np.linalg.qr(np.random.default_rng(2).standard_normal((asm.n, asm.n)) + 0j)
     full = rom.project(asm, Q, F, rc)
     assert rom.full_residual(asm, Q, full, F, [140.0]).max() < 1e-6
+
+
+def test_windows_reuse_the_enclosing_windows_points():
+    """With reuse, the two halves of a bisected window start from the whole window's
+    expansion points in their bands, in the order they were chosen; without reuse they
+    start from their own quarter midpoints.  Both partitions cover the band."""
+    w, asm, F, rc = _setup(floor=False)
+    cand = np.arange(40.0, 300.0, 10.0)
+    kw = dict(q=2, kmax=60, tol=1e-6, max_shifts=4, max_windows=2, min_points=3)
+    quarter = [float(cand[int(np.argmin(np.abs(cand - (cand[0] + (cand[-1] - cand[0]) * (qq + 0.5) / 4.0))))])
+               for qq in range(4)]
+    root, _, _, hist = rom.greedy(asm, F, rc, cand, 2, 60, 1e-6, 4, initial_hz=quarter)
+    assert hist[-1] > 1e-6   # the whole band is bisected
+    for reuse in (False, True):
+        wins = rom.windows(asm, F, rc, cand, reuse=reuse, **kw)
+        assert len(wins) == 2
+        covered = [x for win in wins for x in cand if win["lo"] <= x <= win["hi"]]
+        assert covered == list(cand)
+        for win in wins:
+            inband = [sh for sh in root if win["lo"] <= sh <= win["hi"]]
+            if reuse:
+                assert inband and win["reused"] == len(inband)
+                assert win["shifts"][:len(inband)] == inband
+            else:
+                assert win["reused"] == 0
