@@ -88,16 +88,6 @@ __device__ __forceinline__ double2 a_entry_ld(const DevModel& m, int64_t e, doub
     return make_double2(fma(-w2, mm, fma(-w, d.y, k.x)), fma(w, d.x, k.y));
 }
 
-// element c of a register array indexed by a runtime value (unrolled select: no local memory)
-template <int N, typename T>
-__device__ __forceinline__ T pick(const T (&a)[N], int c) {
-    T v = a[0];
-#pragma unroll
-    for (int q = 1; q < N; ++q)
-        if (q == c) v = a[q];
-    return v;
-}
-
 inline int device_sms() {
     static int sms = 0;
     if (!sms) {
