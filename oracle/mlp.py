@@ -24,6 +24,23 @@ SHAPES = {"W1": (64, 5), "b1": (64,), "W2": (64, 64), "b2": (64,), "W3": (1, 64)
 N_PARAMS = sum(int(np.prod(s)) for s in SHAPES.values())
 
 
+def features(cand_hz, shifts_hz, est, lo: float, hi: float) -> np.ndarray:
+    """Estimator inputs per candidate frequency (one row of 5): the position in the band
+    (f - lo) / (hi - lo); the distances to the three nearest expansion points over the band
+    width, capped at 1 (1 where there are fewer points); log10 of the residual estimate
+    (floored at 1e-16) over 4."""
+    cand = np.asarray(cand_hz, dtype=float)
+    sh = np.asarray(shifts_hz, dtype=float)
+    span = hi - lo if hi > lo else 1.0
+    X = np.ones((cand.size, 5))
+    X[:, 0] = (cand - lo) / span
+    for i, f in enumerate(cand):
+        d = np.sort(np.abs(f - sh) / span)[:3]
+        X[i, 1:1 + d.size] = np.minimum(d, 1.0)
+    X[:, 4] = np.log10(np.maximum(np.asarray(est, dtype=float), 1e-16)) / 4.0
+    return X
+
+
 def unflatten(flat: np.ndarray) -> Dict[str, np.ndarray]:
     """Parameters from the flat vector [W1 (row-major), b1, W2, b2, W3, b3]."""
     out, o = {}, 0

@@ -2,6 +2,7 @@
 central finite differences, Adam's first step against its closed form, the forward
 pass on weights with a closed-form output, and training on a smooth target."""
 import numpy as np
+import pytest
 
 import workloads as W
 from oracle import mlp
@@ -74,3 +75,29 @@ def test_half_weights_round_only_the_matrices():
     assert np.array_equal(q["b1"], p["b1"])
     assert np.abs(q["W2"] - p["W2"]).max() <= np.abs(p["W2"]).max() * 2.0 ** -11
     assert mlp.N_PARAMS == 64 * 5 + 64 + 64 * 64 + 64 + 64 + 1
+
+
+def test_features_pins_and_library_host_code():
+    """Estimator inputs: a candidate on an expansion point has distance 0 to it; missing
+    points read as distance 1; the band ends map to 0 and 1; the residual estimate enters
+    as log10(est)/4.  The library's host routine (rom_features, C++) gives the same values
+    in FP32."""
+    cand = np.array([10.0, 12.5, 20.0, 30.0])
+    sh = [12.5, 28.0]
+    est = np.array([1e-4, 1e-20, 1.0, 3e-2])
+    X = mlp.features(cand, sh, est, 10.0, 30.0)
+    assert X.shape == (4, 5)
+    assert X[0, 0] == 0.0 and X[3, 0] == 1.0
+    assert X[1, 1] == 0.0 and X[1, 2] == pytest.approx(15.5 / 20.0) and X[1, 3] == 1.0
+    assert X[0, 1] == pytest.approx(2.5 / 20.0) and X[0, 2] == pytest.approx(18.0 / 20.0)
+    assert X[0, 4] == pytest.approx(-1.0) and X[1, 4] == pytest.approx(-4.0) and X[2, 4] == 0.0
+    from paper_2310_04734_gb300 import api
+    rng = np.random.default_rng(5)
+    cand = np.sort(rng.uniform(1.0, 800.0, 200))
+    sh = rng.uniform(1.0, 800.0, 7)
+    est = 10.0 ** rng.uniform(-12, 1, 200)
+    got = api.rom_features(cand, sh, est, cand[0], cand[-1])
+    ref = mlp.features(cand, sh, est, cand[0], cand[-1])
+    assert np.allclose(got, ref, rtol=2e-7, atol=2e-7)
+    one = api.rom_features(cand[:5], sh[:1], est[:5], cand[0], cand[-1])
+    assert np.all(one[:, 2:4] == 1.0)
