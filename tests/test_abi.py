@@ -83,3 +83,28 @@ def test_dims_config_sizes(lib):
     for make, n, b in ((W.config1, 2368, 148), (W.config2, 81792, 852)):
         d = api.fsi_model_dims(make().model)
         assert (d.n, d.b) == (n, b)
+
+
+def test_workspace_queries_of_the_reduced_model_calls(lib):
+    """Host-only workspace queries: the residual check grows with the batch and rejects
+    more than 8 load columns; window reuse adds its moment store (4 * max_shifts * q * nrhs
+    columns of n complex128) to the window workspace."""
+    import ctypes as C
+    from paper_2310_04734_gb300 import _lib as L
+    from paper_2310_04734_gb300 import api
+    dims = api.fsi_model_dims(W.config1().model)
+    n = int(dims.n)
+    a, b = C.c_size_t(), C.c_size_t()
+    assert lib.rom_residual_check_workspace(C.byref(dims), 40, 2, 4, C.byref(a)) == 0
+    assert lib.rom_residual_check_workspace(C.byref(dims), 40, 2, 8, C.byref(b)) == 0
+    assert b.value > a.value >= 2 * 4 * 2 * n * 16
+    assert lib.rom_residual_check_workspace(C.byref(dims), 40, 9, 4, C.byref(a)) != 0
+    o = L.fsi_window_opts()
+    o.greedy.q, o.greedy.kmax, o.greedy.max_shifts, o.greedy.tol = 3, 60, 4, 1e-6
+    o.greedy.build = api._rom_opts()
+    o.max_windows, o.min_points = 4, 3
+    o.reuse = 0
+    assert lib.rom_windows_workspace(C.byref(dims), 2, C.byref(o), C.byref(a)) == 0
+    o.reuse = 1
+    assert lib.rom_windows_workspace(C.byref(dims), 2, C.byref(o), C.byref(b)) == 0
+    assert b.value - a.value >= 4 * 4 * 3 * 2 * n * 16
