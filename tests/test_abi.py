@@ -108,3 +108,55 @@ def test_workspace_queries_of_the_reduced_model_calls(lib):
     o.reuse = 1
     assert lib.rom_windows_workspace(C.byref(dims), 2, C.byref(o), C.byref(b)) == 0
     assert b.value - a.value >= 4 * 4 * 3 * 2 * n * 16
+
+
+def test_invalid_arguments_are_rejected_before_device_work(lib):
+    """Empty, out-of-range and degenerate arguments return FSI_EINVAL with a message
+    before any CUDA call (this machine has no GPU, so a CUDA call would fail otherwise)."""
+    import ctypes as C
+    from paper_2310_04734_gb300 import _lib as L
+    from paper_2310_04734_gb300 import api
+    dims = api.fsi_model_dims(W.config1().model)
+    buf = np.zeros(64, np.float64)                       # stands in for every data pointer
+    p = buf.ctypes.data_as(C.c_void_p)
+    dp = buf.ctypes.data_as(L.c_double_p)
+    f_ok = np.array([50.0, 60.0])
+    f_bad = np.array([50.0, -1.0])
+    rcv = np.array([0, 5, dims.n + 3], np.int32)
+    stats = L.fsi_sweep_stats()
+
+    def sweep(f, nf, nrhs, opts, r=p, nrcv=2):
+        return lib.frf_sweep_full(C.byref(dims), p, f.ctypes.data_as(L.c_double_p), nf, p, nrhs, r, nrcv,
+                                  C.byref(opts), p, 1 << 20, p, None, None, None, C.byref(stats), None)
+
+    def last():
+        return lib.fsi_last_error().decode()
+
+    o = L.fsi_solve_opts(precision=1, batch=4, max_refine=10, tol=1e-10)
+    assert sweep(f_ok, 0, 1, o) == -1 and "positive" in last()
+    assert sweep(f_ok, 2, 0, o) == -1
+    assert sweep(f_bad, 2, 1, o) == -1 and "> 0" in last()
+    bad_prec = L.fsi_solve_opts(precision=99, batch=4, max_refine=10, tol=1e-10)
+    assert sweep(f_ok, 2, 1, bad_prec) == -1 and "precision" in last()
+    host = L.fsi_solve_opts(precision=1, batch=4, max_refine=10, tol=1e-10, host_io=1)
+    assert sweep(f_ok, 2, 1, host, r=rcv.ctypes.data_as(C.c_void_p), nrcv=3) == -1 and "receiver" in last()
+    assert lib.fsi_residual(C.byref(dims), p, dp, 1, p, p, 0, p, None) == -1
+    ipiv = np.zeros(8, np.int32)
+    nsing = C.c_int(0)
+    assert lib.fsi_batched_lu(1, 1, 4, 4, 5, p, 4, 16, ipiv.ctypes.data_as(C.c_void_p), p, 1024, C.byref(nsing),
+                              None) == -1 and "shape" in last()
+    assert lib.rom_residual_check(C.byref(dims), p, p, 4, p, p, p, p, p, 9, dp, 1, 1, p, 1 << 20, dp, None) == -1
+    assert lib.rom_sweep(4, p, p, p, p, p, 1, 1, dp, 0, 1, p, 1 << 20, p, None, None) == -1
+    o = L.fsi_window_opts()
+    o.greedy.q, o.greedy.kmax, o.greedy.max_shifts, o.greedy.tol = 2, 20, 3, 1e-6
+    o.greedy.build = api._rom_opts()
+    o.max_windows, o.min_points, o.reuse = 2, 2, 1
+    cand = np.array([40.0, 30.0, 50.0])
+    nw = C.c_int(0)
+    out_d = np.zeros(4)
+    out_i = np.zeros(4, np.int32)
+    assert lib.rom_windows(C.byref(dims), p, p, 1, cand.ctypes.data_as(L.c_double_p), 3, C.byref(o), p, 1 << 20,
+                           p, 1, p, p, p, p, p, C.byref(nw), out_d.ctypes.data_as(L.c_double_p),
+                           out_d.ctypes.data_as(L.c_double_p), out_i.ctypes.data_as(L.c_int32_p),
+                           out_i.ctypes.data_as(L.c_int32_p), out_d.ctypes.data_as(L.c_double_p),
+                           out_i.ctypes.data_as(L.c_int32_p), None) == -1 and "increasing" in last()
