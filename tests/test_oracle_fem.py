@@ -166,3 +166,65 @@ def test_damping_enters_as_complex_stiffness():
     assert np.allclose(ratio[np.abs(ratio) > 0], 0.02, rtol=1e-12)
     fl = asm.is_fluid
     assert np.abs(asm.K[fl][:, fl].toarray().imag).max() == 0.0
+
+
+def test_element_shape_functions_and_matrices_closed_forms():
+    """Element-level pins: trilinear / bilinear shape functions interpolate the nodes and
+    sum to one; the unit-cube Laplacian and mass have the textbook diagonal 1/3 and 1/27
+    and sum to 0 and the volume; the surface mass of a tilted rectangle sums to its area
+    with diagonal area/9 and opposite-corner entry area/36."""
+    rng = np.random.default_rng(0)
+    for a, node in enumerate(fem.HEX_NODES):
+        N, _ = fem.hex8_shape(*node)
+        assert np.allclose(N, np.eye(8)[a])
+    for _ in range(5):
+        N, dN = fem.hex8_shape(*rng.uniform(-1, 1, 3))
+        assert N.sum() == pytest.approx(1.0) and np.allclose(dN.sum(axis=0), 0.0)
+        N, dN = fem.quad4_shape(*rng.uniform(-1, 1, 2))
+        assert N.sum() == pytest.approx(1.0) and np.allclose(dN.sum(axis=0), 0.0)
+    X = (fem.HEX_NODES + 1.0) / 2.0                       # unit cube
+    Ke, Me = fem.hex8_matrices(X)
+    assert np.allclose(np.diag(Ke), 1.0 / 3.0) and np.allclose(Ke @ np.ones(8), 0.0)
+    assert np.allclose(np.diag(Me), 1.0 / 27.0) and Me.sum() == pytest.approx(1.0)
+    Xb = X * np.array([0.5, 2.0, 3.0])                    # box: Laplacian scales, mass sums to the volume
+    Ke_b, Me_b = fem.hex8_matrices(Xb)
+    assert Me_b.sum() == pytest.approx(3.0) and np.allclose(Ke_b @ np.ones(8), 0.0)
+    a, b = 0.7, 1.9
+    R = la.expm(np.array([[0, -0.3, 0.2], [0.3, 0, -0.5], [-0.2, 0.5, 0]]))   # a rotation
+    Xq = np.array([[0, 0, 0], [a, 0, 0], [a, b, 0], [0, b, 0]], dtype=float) @ R.T + 1.5
+    Mq = fem.quad4_surface_mass(Xq)
+    assert Mq.sum() == pytest.approx(a * b)
+    assert np.allclose(np.diag(Mq), a * b / 9.0) and Mq[0, 2] == pytest.approx(a * b / 36.0)
+
+
+def test_mitc4_plate_rigid_modes_and_mass():
+    """The Reissner-Mindlin element (shear strain grad w + beta) stores no energy in the
+    three rigid modes of a plate: translation w = 1, and rotations w = s with beta_s = -1,
+    w = z with beta_z = -1; its translational mass is rho t times the area; a pure bending
+    field (w = s^2 / 2, beta_s = -s) is not rigid."""
+    X2 = np.array([[0.0, 0.0], [0.8, 0.1], [0.9, 1.1], [-0.1, 0.9]])
+    Ke, Me = fem.mitc4_plate(X2, 60e9, 0.3, 1600.0, 0.002)
+    assert np.allclose(Ke, Ke.T, rtol=1e-12, atol=1e-9 * np.abs(Ke).max())
+    modes = []
+    u = np.zeros(12); u[0::3] = 1.0; modes.append(u)
+    u = np.zeros(12); u[0::3] = X2[:, 0]; u[1::3] = -1.0; modes.append(u)
+    u = np.zeros(12); u[0::3] = X2[:, 1]; u[2::3] = -1.0; modes.append(u)
+    scale = np.abs(Ke).max()
+    for u in modes:
+        assert np.abs(Ke @ u).max() < 1e-9 * scale
+    d1, d2 = X2[2] - X2[0], X2[3] - X2[1]
+    area = 0.5 * abs(d1[0] * d2[1] - d1[1] * d2[0])
+    w = np.zeros(12); w[0::3] = 1.0
+    assert w @ Me @ w == pytest.approx(1600.0 * 0.002 * area, rel=1e-12)
+    u = np.zeros(12); u[0::3] = X2[:, 0] ** 2 / 2.0; u[1::3] = -X2[:, 0]
+    assert u @ Ke @ u > 1e-6 * scale
+
+
+def test_ring_nodes_walk_the_perimeter_counter_clockwise():
+    for nx, ny in ((3, 4), (8, 8), (24, 24)):
+        ring = fem.ring_nodes(nx, ny)
+        assert len(ring) == 2 * nx + 2 * ny - 4 == len(set(ring))
+        assert ring[0] == (0, 0) and ring[1] == (1, 0) and ring[-1] == (0, 1)
+        assert all(i in (0, nx - 1) or j in (0, ny - 1) for i, j in ring)
+        steps = [abs(a[0] - b[0]) + abs(a[1] - b[1]) for a, b in zip(ring, ring[1:] + ring[:1])]
+        assert steps == [1] * len(ring)
