@@ -119,3 +119,23 @@ def test_sweep_shapes(small):
     w, asm, F, rc = small
     p, L = fom.sweep(asm, [50.0, 60.0], F, rc, method="dense")
     assert p.shape == (2, len(rc), w.n_rhs) and L.shape == p.shape
+
+
+def test_golden_fixture_reproduces_from_the_oracle():
+    """tests/golden/cfg1_fom.json (written by tests/golden/make_golden.py from the oracle
+    only) matches a fresh oracle solve at sampled frequencies, for the same workload,
+    receivers and frequency grid."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "cfg1_fom.json")))
+    w = W.config1()
+    assert g["workload"] == w.name and g["freqs_hz"] == w.freqs_hz.tolist()
+    assert [tuple(r) for r in g["receivers"]] == [tuple(r) for r in w.receivers]
+    asm = fem.assemble(w.model)
+    F = fem.load_matrix(w.model, w.loads, w.n_rhs)
+    rc = fem.receiver_dofs(w.model, w.receivers)
+    idx = [0, 57, 180]
+    p, _ = fom.sweep(asm, w.freqs_hz[idx], F, rc, method="dense")
+    stored = np.array(g["p_re"])[idx] + 1j * np.array(g["p_im"])[idx]
+    assert np.abs(p - stored).max() <= 1e-12 * np.abs(stored).max()
+    assert all(k >= 1.0 for k in g["kappa1_scaled"])
