@@ -81,12 +81,21 @@ def _soar(asm, lu, omega_j, f, q):
     A = -Kt^-1 Dt, B = -Kt^-1 M, starting vector u = -Kt^-1 f.  Returns an
     orthonormal basis of span{r_0, ..., r_{q-1}} with r_1 = A r_0,
     r_m = A r_{m-1} + B r_{m-2}.
+
+    Each step forms r = A q_j + B p_j and the companion s = q_j, orthogonalises
+    r against the q's (the same coefficients update s against the p's) and
+    normalises both by |r|.  Deflation (|r| at rounding level, r already in
+    the span): Bai and Su continue with q_{j+1} = 0 and p_{j+1} = s, so the
+    sequence can still reach new directions later; the process breaks down
+    (stops) only when s also lies in the span of the p vectors of earlier
+    deflations.  Zero q's are not part of the returned basis.
     """
     Dt = 2j * omega_j * asm.M + asm.D
     u = -lu.solve(f)
     nu = np.linalg.norm(u)
     Q = [u / nu]
     P = [np.zeros_like(u)]
+    deflated = []          # indices j with q_j = 0
     for j in range(q - 1):
         r = -lu.solve(Dt @ Q[j] + asm.M @ P[j])
         s = Q[j].copy()
@@ -95,11 +104,25 @@ def _soar(asm, lu, omega_j, f, q):
             r = r - t * Q[i]
             s = s - t * P[i]
         t = np.linalg.norm(r)
-        if t <= DEFLATION_TOL * nu:
+        if t > DEFLATION_TOL * nu:
+            Q.append(r / t)
+            P.append(s / t)
+            continue
+        # deflation: breakdown if s is in span{p_i : q_i = 0} (for none: s = 0)
+        ns = np.linalg.norm(s)
+        if deflated:
+            Pd = np.stack([P[i] for i in deflated], axis=1)
+            coef, *_ = np.linalg.lstsq(Pd, s, rcond=None)
+            rest = np.linalg.norm(s - Pd @ coef)
+        else:
+            rest = ns
+        if rest <= DEFLATION_TOL * max(ns, 1.0):
             break
-        Q.append(r / t)
-        P.append(s / t)
-    return np.stack(Q, axis=1)
+        Q.append(np.zeros_like(u))
+        P.append(s)
+        deflated.append(j + 1)
+    keep = [Q[i] for i in range(len(Q)) if i not in deflated]
+    return np.stack(keep, axis=1)
 
 
 def has_damping_matrix(asm) -> bool:

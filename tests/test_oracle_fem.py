@@ -228,3 +228,109 @@ def test_ring_nodes_walk_the_perimeter_counter_clockwise():
         assert all(i in (0, nx - 1) or j in (0, ny - 1) for i, j in ring)
         steps = [abs(a[0] - b[0]) + abs(a[1] - b[1]) for a, b in zip(ring, ring[1:] + ring[:1])]
         assert steps == [1] * len(ring)
+
+
+# --------------------------------------------------------------------------- floor impedance
+def _floor_pressure_energy(spec, p_nodes):
+    """int_floor |p|^2 dGamma of the bilinear interpolant of nodal pressures on y = 0, by
+    the closed form of the bilinear element's mass on an hx x hz rectangle
+    (hx hz / 36) [4 2 1 2; 2 4 2 1; 1 2 4 2; 2 1 2 4], written out here independently of the
+    oracle's quadrature."""
+    hx = spec.Lx / (spec.nx - 1)
+    hz = spec.Lz / (spec.nz - 1)
+    Me = hx * hz / 36.0 * np.array([[4, 2, 1, 2], [2, 4, 2, 1], [1, 2, 4, 2], [2, 1, 2, 4]], float)
+    tot = 0.0
+    for k in range(spec.nz - 1):
+        for i in range(spec.nx - 1):
+            v = np.array([p_nodes[i, k], p_nodes[i + 1, k], p_nodes[i + 1, k + 1], p_nodes[i, k + 1]])
+            tot += float(np.real(np.conj(v) @ Me @ v))
+    return tot
+
+
+def _power_balance(asm, spec, w, freq, flip_damping=False):
+    """Time-averaged power injected by the unit shell force and absorbed by the floor."""
+    num = fem.Numbering(spec)
+    om = 2 * np.pi * freq
+    A = (asm.K + (-1j if flip_damping else 1j) * om * asm.D - om ** 2 * asm.M).tocsc()
+    F = fem.load_matrix(spec, w.loads, w.n_rhs)[:, 0]
+    import scipy.sparse.linalg as spla
+    x = spla.spsolve(A, F)
+    a = np.flatnonzero(F)[0]
+    # e^{+i w t}: shell velocity i w x_a; P_in = 1/2 Re(conj(v_a) F_a)
+    p_in = 0.5 * np.real(np.conj(1j * om * x[a]) * F[a])
+    p_floor_nodes = np.array([[x[num.p(i, 0, k)] for k in range(spec.nz)] for i in range(spec.nx)])
+    # locally reacting wall: normal velocity into the wall v_n = p / Z, P = 1/2 Re(p conj(v_n))
+    p_floor = 0.5 * np.real(1.0 / np.conj(spec.Z_floor)) * _floor_pressure_energy(spec, p_floor_nodes)
+    return p_in, p_floor
+
+
+def test_power_balance_of_the_floor_impedance():
+    """With the shell undamped (eta = 0) the floor impedance (Re Z > 0) is the only loss: the
+    power the point force injects, 1/2 Re(conj(i w w_a) F_a), equals the power the floor
+    absorbs, 1/2 Re(1/Z) int_floor |p|^2, and is positive (paper Sec. 2 problem statement,
+    Eq. 8 damping term).  The identity holds exactly for the discrete system (the shell's and
+    cavity's stiffness and mass forms are real symmetric and the coupling enters the shell and
+    fluid rows with the signs of the weak form), so any slip in the sign of i w D, in the sign
+    of the coupling or in rho/Z breaks it.  A flipped damping term is planted to show it."""
+    spec = W.ModelSpec(Lx=0.6, Ly=0.5, Lz=0.8, nx=5, ny=4, nz=6, eta=(0.0,),
+                       Z_floor=W.AIR_RHO * W.AIR_C * (1.5 - 0.7j))
+    w = W.Workload(name="power-balance", config_id=91, model=spec,
+                                  loads=(W.PointLoad(slab=2, ring=3, column=0),), n_rhs=1, receivers=((1, 1, 1),),
+                                  freqs_hz=np.array([1.0]))
+    asm = fem.assemble(spec)
+    for f in (61.0, 143.0, 377.0):
+        p_in, p_floor = _power_balance(asm, spec, w, f)
+        assert p_in > 0.0
+        assert abs(p_in - p_floor) <= 1e-9 * p_in, (f, p_in, p_floor)
+        bad_in, bad_floor = _power_balance(asm, spec, w, f, flip_damping=True)
+        assert bad_in < 0.0 and abs(bad_in - bad_floor) > 0.5 * abs(bad_floor)
+
+
+def test_impedance_tube_closed_form():
+    """The cavity block alone (rigid side walls, no shell) driven by a uniform normal pressure
+    gradient g on the face y = Ly, with the locally reacting impedance Z on y = 0, is a 1-D
+    problem: p(y) = a cos(ky) + b sin(ky), p'(0) = i k (rho c / Z) p(0) (the floor condition
+    dp/dn = -i w rho p / Z, n = -y), p'(Ly) = g.  The trilinear solution converges to it at
+    O(h^2); the reactive part of Z enters the phase, so a conjugated Z (rho / conj(Z)) or a
+    flipped damping sign misses it by orders of magnitude."""
+    import scipy.sparse.linalg as spla
+    Z = W.AIR_RHO * W.AIR_C * (0.8 + 1.3j)
+    f, g, Ly = 150.0, 1.0, 1.0
+    om = 2 * np.pi * f
+    k = om / W.AIR_C
+    a = g / (k * (-np.sin(k * Ly) + 1j * (W.AIR_RHO * W.AIR_C / Z) * np.cos(k * Ly)))
+    b = 1j * (W.AIR_RHO * W.AIR_C / Z) * a
+
+    def exact(y):
+        return a * np.cos(k * y) + b * np.sin(k * y)
+
+    def solve(ny, variant=None):
+        spec = W.ModelSpec(Lx=0.3, Ly=Ly, Lz=0.4, nx=3, ny=ny, nz=3, eta=(0.0,), Z_floor=Z)
+        asm = fem.assemble(spec)
+        fl = np.flatnonzero(asm.is_fluid)
+        D = asm.D[fl][:, fl]
+        if variant == "conj":
+            D = D.conj()
+        sgn = -1j if variant == "flip" else 1j
+        A = (asm.K[fl][:, fl] + sgn * om * D - om ** 2 * asm.M[fl][:, fl]).tocsc()
+        num = fem.Numbering(spec)
+        # consistent load of a uniform g on the top face: g times the nodal tributary areas
+        hx, hz = spec.Lx / (spec.nx - 1), spec.Lz / (spec.nz - 1)
+        rhs = np.zeros(spec.n, complex)
+        for kk in range(spec.nz):
+            for i in range(spec.nx):
+                wx = 0.5 if i in (0, spec.nx - 1) else 1.0
+                wz = 0.5 if kk in (0, spec.nz - 1) else 1.0
+                rhs[num.p(i, ny - 1, kk)] = g * hx * hz * wx * wz
+        p = spla.spsolve(A, rhs[fl])
+        full = np.zeros(spec.n, complex)
+        full[fl] = p
+        ys = np.linspace(0.0, Ly, ny)
+        got = np.array([full[num.p(1, j, 1)] for j in range(ny)])
+        return np.abs(got - exact(ys)).max() / np.abs(exact(ys)).max()
+
+    e1, e2 = solve(33), solve(65)
+    print("impedance tube errors", e1, e2)
+    assert e2 < 1e-3 and 3.0 < e1 / e2 < 5.0        # O(h^2)
+    assert solve(65, "conj") > 100 * e2
+    assert solve(65, "flip") > 100 * e2

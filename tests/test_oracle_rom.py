@@ -69,6 +69,66 @@ def test_soar_basis_spans_second_order_moments():
     assert _span_gap(V, R) < 1e-6
 
 
+class _Identity:
+    """Stands in for the factor of Kt = I (so A = -Dt and B = -M in SOAR)."""
+
+    @staticmethod
+    def solve(x):
+        return np.array(x, dtype=complex)
+
+
+class _Pencil:
+    def __init__(self, M, D):
+        self.M = M
+        self.D = D
+
+
+def _explicit_second_order(Dt, M, u, q):
+    """Orthonormal basis of span{r_0..r_{q-1}} (rank-revealing SVD: the sequence is dependent)."""
+    r = [u, -Dt @ u]
+    for _ in range(2, q):
+        r.append(-Dt @ r[-1] - M @ r[-2])
+    R = np.stack(r[:q], axis=1)
+    U, sv, _ = np.linalg.svd(R, full_matrices=False)
+    return U[:, :int((sv > 1e-12 * sv[0]).sum())]
+
+
+def test_soar_deflation_continues_as_bai_and_su():
+    """SOAR's deflation branch (Bai and Su 2005, the reference of Eq. 9): r_1 = A r_0 is parallel
+    to r_0, so the step deflates; the recurrence must continue with q = 0 and p = s, because
+    r_2 = A r_1 + B r_0 brings in a new direction (B e1 = e2) and r_3 another (A e2 = e3).
+    Stopping at the deflation would return span{e1} only.  The explicit sequence fixes the span."""
+    n, alpha, gamma = 6, 0.7, 1.9
+    D = np.zeros((n, n), complex)
+    M = np.zeros((n, n), complex)
+    D[0, 0] = -alpha              # A e1 = alpha e1
+    M[1, 0] = -1.0                # B e1 = e2
+    D[2, 1] = -gamma              # A e2 = gamma e3
+    f = np.zeros(n, complex)
+    f[0] = -1.0                   # u = -Kt^-1 f = e1
+    q = 4
+    V = rom._soar(_Pencil(M, D), _Identity(), 0.0, f, q)
+    R = _explicit_second_order(D, M, -f, q)
+    assert V.shape[1] == 3 == R.shape[1]
+    assert np.abs(V.conj().T @ V - np.eye(3)).max() < 1e-14
+    assert _span_gap(V, R) < 1e-12
+
+
+def test_soar_breakdown_when_the_sequence_stays_in_the_span():
+    """If after a deflation s also lies in the span of the deflated p vectors, the sequence can
+    bring nothing new (here B e1 = 0, so every r_m is a multiple of e1): SOAR stops there."""
+    n = 5
+    D = np.zeros((n, n), complex)
+    M = np.zeros((n, n), complex)
+    D[0, 0] = -0.4
+    f = np.zeros(n, complex)
+    f[0] = 2.0
+    V = rom._soar(_Pencil(M, D), _Identity(), 0.0, f, 5)
+    R = _explicit_second_order(D, M, -f, 5)
+    assert V.shape[1] == 1 == R.shape[1]
+    assert _span_gap(V, R) < 1e-12
+
+
 @pytest.mark.parametrize("floor", [False, True])
 def test_rom_interpolates_at_expansion_points(floor):
     """The ROM reproduces the FOM output at every expansion point (moment matching of
