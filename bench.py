@@ -530,7 +530,7 @@ def main():
     # 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    g = 0
+    g = 10 if args.precision == "tf32x3_ir" else 0
     achieved = kern_flops[g] / (kern_ms[g] / 1e3) / 1e12 if kern_ms[g] > 0 else None
     if args.precision == "tf32x3_ir":
         # tensor pipe: TF32 dense peak = half the measured BF16 burst peak (nominal ratio 1:2);
@@ -555,7 +555,7 @@ def main():
     shares = {k: {"ms": float(kern_ms[i]), "launches": int(kern_n[i]),
                   "share": float(kern_ms[i] / max(kern_ms.sum(), 1e-9))}
               for i, k in enumerate(["gemm", "panel", "trsm", "laswp", "form", "shift", "solve_tri", "resid",
-                                         "solve_gemv"])}
+                                         "solve_gemv", "pack", "tcgemm"])}
 
     if rank == 0:
         cpu = None

@@ -123,7 +123,7 @@ enum { FSI_REFINE_IR = 0, FSI_REFINE_GMRES = 1 };
 
 /* Kernel classes of the per-kernel totals in fsi_sweep_stats. */
 enum {
-    FSI_K_GEMM = 0,               /* trailing complex GEMM update of the band LU    */
+    FSI_K_GEMM = 0,               /* complex GEMM updates of the band LU (FP32/FP64 pipe) */
     FSI_K_PANEL = 1,              /* panel LU with partial pivoting                 */
     FSI_K_TRSM = 2,               /* unit-lower triangular solve of pivot rows      */
     FSI_K_LASWP = 3,              /* row interchanges                               */
@@ -132,7 +132,9 @@ enum {
     FSI_K_SOLVE = 6,              /* triangles of the forward / backward slab solves */
     FSI_K_RESID = 7,              /* FP64 residual, refinement updates, receivers   */
     FSI_K_GEMV = 8,               /* off-diagonal factor blocks in the slab solves  */
-    FSI_K_COUNT = 9,
+    FSI_K_PACK = 9,               /* hi/lo operand split of the tensor-core updates */
+    FSI_K_TCGEMM = 10,            /* trailing updates on the tcgen05 tensor cores    */
+    FSI_K_COUNT = 11,
     FSI_K_SLOTS = 12              /* array length in fsi_sweep_stats (room to grow) */
 };
 
@@ -191,13 +193,26 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
  * complement (cols >= npiv); ipiv[i*npiv + j] is the row swapped with row j
  * (LAPACK getrf convention, 0-based).  precision selects FP64 or FP32 data:
  * A points to fsi_c64 (FP64) or to {float re, im} pairs (FSI_FP32_IR, and
- * FSI_TF32X3_IR with the tensor-core trailing updates).  ws: device
- * workspace of fsi_lu_workspace bytes.  status_out (host, nullable) gets the
- * number of matrices that met a zero or non-finite pivot. */
-fsi_status fsi_lu_workspace(int batch, int m, size_t* bytes);
+ * FSI_TF32X3_IR with the large trailing updates on the tensor cores; those
+ * need ld, sA and the first column right of each update even, otherwise they
+ * run on the FP32 SIMT pipe).  ws: device workspace of fsi_lu_workspace
+ * bytes for the same precision and sizes.  n_singular_out (host, nullable)
+ * gets the number of matrices that met a zero or non-finite pivot.  Any other
+ * precision value is rejected with FSI_EINVAL.  FSI_TF32X3_IR synchronizes
+ * the stream and returns FSI_ETIMEOUT when a bounded wait of a tensor-core
+ * kernel gave up (see fsi_set_wait_limit); the factors are then invalid. */
+fsi_status fsi_lu_workspace(int precision, int batch, int m, int ncols, int npiv, size_t* bytes);
 fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, void* A, int64_t ld,
                           int64_t sA, int32_t* ipiv, void* ws, size_t ws_bytes,
                           int* n_singular_out, void* stream);
+
+/* Spin limit of the bounded mbarrier waits in the tensor-core kernels: the
+ * number of polls after which a kernel gives up, records FSI_ETIMEOUT, waits
+ * for the loads and MMAs it already issued and releases its tensor memory.
+ * 0 restores the default (about 6.7e7 polls, seconds); small values make the
+ * waits run out on purpose (tests of the timeout path).  Process-wide, host
+ * only.  Errors: FSI_EINVAL (negative). */
+fsi_status fsi_set_wait_limit(int64_t spins);
 
 /* Allocation-free variant of fsi_batched_lu (the paper has no counterpart; it
  * is a service to callers).  Some callers cannot allocate device memory: code
@@ -210,13 +225,19 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
  * library holds until the process exits.
  *   - batch is limited to 4095 matrices; larger batches return FSI_EINVAL
  *     with a message (split the call, or use fsi_batched_lu).
- *   - The first call on each device looks up the array's device address with
- *     that device current; make that first call before any stream capture.
+ *   - precision is FSI_FP64 or FSI_FP32_IR.  FSI_TF32X3_IR is rejected with
+ *     FSI_EINVAL: its tensor-core updates need an operand workspace that
+ *     grows with the matrices (use fsi_batched_lu).  Other values are
+ *     rejected too.
+ *   - Every call looks up the array's device address for the current device
+ *     (a host-side lookup, no allocation).  The first call on a device also
+ *     loads the library's device code there: make it before any stream
+ *     capture.
  *   - All calls share the one array and each call clears the part it uses
  *     before use: calls that overlap on the GPU (different streams, or
  *     different host threads on one device) race and must be serialised.
- * Arguments, results and errors are those of fsi_batched_lu; it synchronizes
- * the stream when n_singular_out is not NULL. */
+ * Otherwise arguments, results and errors are those of fsi_batched_lu; it
+ * synchronizes the stream when n_singular_out is not NULL. */
 fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, int ncols, int npiv, void* A,
                                   int64_t ld, int64_t sA, int32_t* ipiv, int* n_singular_out,
                                   void* stream);
@@ -255,18 +276,28 @@ fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64*
                        size_t ws_bytes, fsi_c64* KR, fsi_c64* DR, fsi_c64* MR, fsi_c64* fR,
                        fsi_c64* CR, void* stream);
 
-/* Workspace bytes for rom_sweep. */
-fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, size_t* bytes);
+/* Workspace bytes for rom_sweep with this precision (FSI_FP64 or FSI_FP32_IR). */
+fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, int precision, size_t* bytes);
 
 /* Reduced sweep (Eq. 11): y_R(w) = C_R (K_R + i w D_R - w^2 M_R)^-1 f_R for nf
- * frequencies, batched `batch` at a time, each reduced system equilibrated
- * (row then column max scaling) and solved by dense LU with partial pivoting
- * in FP64.  Inputs device (column-major), f_hz host; p_out [nf][nrcv][nrhs]
- * device; spl_out same shape, nullable. */
+ * frequencies, `batch` at a time.  Inputs device (column-major), f_hz host;
+ * p_out [nf][nrcv][nrhs] device; spl_out same shape, nullable.
+ *   precision FSI_FP64: each reduced system is equilibrated (row then column
+ *     max scaling) and solved by dense LU with partial pivoting in FP64.
+ *   precision FSI_FP32_IR (k <= 128, nrhs <= 4): the systems run through the
+ *     persistent kernel of rom_multi_sweep (equilibrated LU in FP32, refined
+ *     against the FP64 residual until the correction is at rounding level);
+ *     a frequency whose refinement stalls is solved again by the FP64 path.
+ *   fp64_out (host, nf, nullable): 1 where that FP64 re-solve happened.
+ * The reduced model's error against the full-order model is not estimated
+ * here: rom_greedy returns the residual estimate over its candidates and
+ * rom_residual_check / rom_check_resolve evaluate the full-order residual.
+ * Synchronizes the stream.  Errors: FSI_EINVAL, FSI_ENOMEM, FSI_ESINGULAR. */
 fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR,
                      const fsi_c64* fR, const fsi_c64* CR, int nrhs, int nrcv,
-                     const double* f_hz, int nf, int batch, void* ws, size_t ws_bytes,
-                     fsi_c64* p_out, double* spl_out, void* stream);
+                     const double* f_hz, int nf, int batch, int precision, void* ws,
+                     size_t ws_bytes, fsi_c64* p_out, double* spl_out, int32_t* fp64_out,
+                     void* stream);
 
 /* Workspace bytes for rom_residual_check (batch frequencies at a time). */
 fsi_status rom_residual_check_workspace(const fsi_dims* dims, int k, int nrhs, int batch, size_t* bytes);
@@ -285,6 +316,83 @@ fsi_status rom_residual_check(const fsi_dims* dims, const void* d_model, const f
                               const fsi_c64* fR, const fsi_c64* F, int nrhs, const double* f_hz,
                               int nf, int batch, void* ws, size_t ws_bytes, double* relres,
                               void* stream);
+
+/* Workspace bytes for rom_check_resolve (batch frequencies at a time; full:
+ * the options of the full-order re-solves, host_io must be 0). */
+fsi_status rom_check_resolve_workspace(const fsi_dims* dims, int k, int nrhs, int nrcv, int batch,
+                                       const fsi_solve_opts* full, size_t* bytes);
+
+/* Check and re-solve (paper Sec. 3.3: the reduced model's outputs are only as
+ * good as its error check; the full-order solve stays the fallback).  p_out
+ * and spl_out ([nf][nrcv][nrhs], device) hold the reduced outputs at f_hz
+ * (e.g. from rom_sweep).  For every frequency the reduced solution is lifted,
+ * x = V x_R, and judged by its full-order FP64 residual as rom_residual_check
+ * computes it; a frequency whose largest relative residual over the load
+ * columns exceeds res_tol is solved again at full order by frf_sweep_full with
+ * the options `full` (device buffers), and its rows of p_out / spl_out are
+ * replaced by the full-order outputs.  V, KR/DR/MR/fR, F, rcv: device, as for
+ * rom_residual_check and frf_sweep_full.  Host outputs: relres_out [nf][nrhs]
+ * (nullable), resolved_out [nf] (nullable; 1 where replaced), *n_resolved.
+ * res_tol = 0 re-solves every frequency with a nonzero residual.
+ * Synchronizes the stream.  Errors: FSI_EINVAL, FSI_ENOMEM, FSI_ECUDA,
+ * FSI_ESINGULAR, FSI_ENOCONV (a re-solve missed its tolerance; outputs are
+ * still written). */
+fsi_status rom_check_resolve(const fsi_dims* dims, const void* d_model, const fsi_c64* V, int k,
+                             const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR,
+                             const fsi_c64* fR, const fsi_c64* F, int nrhs, const int32_t* rcv,
+                             int nrcv, const double* f_hz, int nf, int batch, double res_tol,
+                             const fsi_solve_opts* full, void* ws, size_t ws_bytes, fsi_c64* p_out,
+                             double* spl_out, double* relres_out, int32_t* resolved_out,
+                             int* n_resolved, void* stream);
+
+/* Reduced models on disk (the offline / online split of paper Sec. 3.3: the
+ * reduced matrices are built once and reused).  A file holds nwin windows in
+ * the slot layout of rom_windows (nwin = 1 and kmax = k for one model of
+ * rom_project), their frequency ranges and expansion points, and optionally
+ * the projection bases. */
+typedef struct {
+    int nwin;                     /* windows (1 for a single reduced model)        */
+    int kmax;                     /* slot size of the matrix arrays                */
+    int nrhs, nrcv;
+    int64_t n;                    /* rows of the stored bases V; 0: none stored    */
+    int nshift_total;             /* expansion points over all windows             */
+} fsi_rom_info;
+
+typedef struct {
+    fsi_rom_info info;
+    int on_device;                /* 1: the matrix arrays are device pointers,     */
+                                  /* 0: host pointers                              */
+    fsi_c64* KR;                  /* [nwin][kmax*kmax]: window w's k_w x k_w, ld k_w */
+    fsi_c64* DR;
+    fsi_c64* MR;
+    fsi_c64* fR;                  /* [nwin][kmax*nrhs]: k_w x nrhs, ld k_w          */
+    fsi_c64* CR;                  /* [nwin][kmax*nrcv]: nrcv x k_w, ld nrcv         */
+    fsi_c64* V;                   /* [nwin][kmax*n]: n x k_w, ld n (NULL if n = 0)  */
+    double* lo;                   /* host [nwin]: window frequency range, Hz        */
+    double* hi;
+    int32_t* k;                   /* host [nwin]: reduced order of each window      */
+    int32_t* nshift;              /* host [nwin]: expansion points per window       */
+    double* shifts_hz;            /* host [nshift_total], window after window       */
+} fsi_rom_store;
+
+/* Write the model described by `rom` to `path` (version-1 format, a 64-bit
+ * checksum at the end); device arrays are staged through host memory on
+ * `stream`.  Errors: FSI_EINVAL (sizes, NULL arrays, file not writable),
+ * FSI_ECUDA. */
+fsi_status rom_save(const char* path, const fsi_rom_store* rom, void* stream);
+
+/* Sizes of the model in `path` (reads and checks the header only). */
+fsi_status rom_file_info(const char* path, fsi_rom_info* info);
+
+/* Read `path` into the caller's buffers: rom->info gives their capacity
+ * (nwin, kmax, nshift_total at least the file's; nrhs, nrcv equal; n equal
+ * when the file stores bases) and rom->on_device their kind.  Windows go to
+ * the slots of rom->info.kmax; on success rom->info holds the file's sizes
+ * with the caller's kmax, and lo / hi / k / nshift / shifts_hz are filled.
+ * The data round-trips bit for bit.  Errors: FSI_EINVAL (not a model file,
+ * unsupported version, truncated, checksum mismatch, buffers too small),
+ * FSI_ECUDA. */
+fsi_status rom_load(const char* path, fsi_rom_store* rom, void* stream);
 
 /* Greedy expansion points (paper Sec. 3.3; its error measure replaced by a
  * residual estimate, as Sec. 5 suggests).  Options: */

@@ -70,6 +70,17 @@ class fsi_rom_item(C.Structure):
                 ("spl_out", c_void_p)]
 
 
+class fsi_rom_info(C.Structure):
+    _fields_ = [("nwin", c_int), ("kmax", c_int), ("nrhs", c_int), ("nrcv", c_int), ("n", C.c_int64),
+                ("nshift_total", c_int)]
+
+
+class fsi_rom_store(C.Structure):
+    _fields_ = [("info", fsi_rom_info), ("on_device", c_int), ("KR", c_void_p), ("DR", c_void_p), ("MR", c_void_p),
+                ("fR", c_void_p), ("CR", c_void_p), ("V", c_void_p), ("lo", c_double_p), ("hi", c_double_p),
+                ("k", c_int32_p), ("nshift", c_int32_p), ("shifts_hz", c_double_p)]
+
+
 # name -> (restype, argtypes)
 SIGNATURES = {
     "fsi_model_dims": (c_int, [C.POINTER(fsi_model_desc), C.POINTER(fsi_dims)]),
@@ -84,7 +95,8 @@ SIGNATURES = {
                                C.POINTER(fsi_sweep_stats), c_void_p]),
     "fsi_residual": (c_int, [C.POINTER(fsi_dims), c_void_p, c_double_p, c_int, c_void_p, c_void_p,
                              c_int, c_void_p, c_void_p]),
-    "fsi_lu_workspace": (c_int, [c_int, c_int, C.POINTER(c_size_t)]),
+    "fsi_lu_workspace": (c_int, [c_int, c_int, c_int, c_int, c_int, C.POINTER(c_size_t)]),
+    "fsi_set_wait_limit": (c_int, [C.c_int64]),
     "fsi_batched_lu": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, C.c_int64, C.c_int64,
                                c_void_p, c_void_p, c_size_t, C.POINTER(c_int), c_void_p]),
     "fsi_batched_lu_noalloc": (c_int, [c_int, c_int, c_int, c_int, c_int, c_void_p, C.c_int64, C.c_int64,
@@ -97,13 +109,23 @@ SIGNATURES = {
     "rom_project": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_void_p, c_int, c_void_p,
                             c_int, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p, c_void_p,
                             c_void_p, c_void_p]),
-    "rom_sweep_workspace": (c_int, [c_int, c_int, c_int, c_int, C.POINTER(c_size_t)]),
+    "rom_sweep_workspace": (c_int, [c_int, c_int, c_int, c_int, c_int, C.POINTER(c_size_t)]),
     "rom_sweep": (c_int, [c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int,
-                          c_double_p, c_int, c_int, c_void_p, c_size_t, c_void_p, c_void_p, c_void_p]),
+                          c_double_p, c_int, c_int, c_int, c_void_p, c_size_t, c_void_p, c_void_p, c_int32_p,
+                          c_void_p]),
     "rom_residual_check_workspace": (c_int, [C.POINTER(fsi_dims), c_int, c_int, c_int, C.POINTER(c_size_t)]),
     "rom_residual_check": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                                    c_void_p, c_void_p, c_int, c_double_p, c_int, c_int, c_void_p, c_size_t,
                                    c_double_p, c_void_p]),
+    "rom_check_resolve_workspace": (c_int, [C.POINTER(fsi_dims), c_int, c_int, c_int, c_int,
+                                            C.POINTER(fsi_solve_opts), C.POINTER(c_size_t)]),
+    "rom_check_resolve": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                                  c_void_p, c_void_p, c_int, c_void_p, c_int, c_double_p, c_int, c_int, C.c_double,
+                                  C.POINTER(fsi_solve_opts), c_void_p, c_size_t, c_void_p, c_void_p, c_double_p,
+                                  c_int32_p, C.POINTER(c_int), c_void_p]),
+    "rom_save": (c_int, [C.c_char_p, C.POINTER(fsi_rom_store), c_void_p]),
+    "rom_file_info": (c_int, [C.c_char_p, C.POINTER(fsi_rom_info)]),
+    "rom_load": (c_int, [C.c_char_p, C.POINTER(fsi_rom_store), c_void_p]),
     "rom_greedy_workspace": (c_int, [C.POINTER(fsi_dims), c_int, C.POINTER(fsi_greedy_opts),
                                      C.POINTER(c_size_t)]),
     "rom_greedy": (c_int, [C.POINTER(fsi_dims), c_void_p, c_void_p, c_int, c_double_p, c_int, c_double_p,

@@ -208,12 +208,17 @@ def fsi_batched_lu(A, npiv: int, tensor_cores: bool = False):
     prec = FSI_FP64 if A.dtype == torch.complex128 else (FSI_TF32X3_IR if tensor_cores else FSI_FP32_IR)
     ipiv = torch.empty((batch, npiv), dtype=torch.int32, device=A.device)
     need = C.c_size_t()
-    L.check(lib.fsi_lu_workspace(batch, m, C.byref(need)), "fsi_lu_workspace")
+    L.check(lib.fsi_lu_workspace(prec, batch, m, ncols, npiv, C.byref(need)), "fsi_lu_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device=A.device)
     nsing = C.c_int(0)
     L.check(lib.fsi_batched_lu(prec, batch, m, ncols, npiv, _ptr(A), ncols, m * ncols, _ptr(ipiv), _ptr(ws),
                                C.c_size_t(need.value), C.byref(nsing), _stream_ptr()), "fsi_batched_lu")
     return ipiv, nsing.value
+
+
+def fsi_set_wait_limit(spins: int = 0):
+    """Spin limit of the tensor-core kernels' bounded waits (0: the default)."""
+    L.check(L.load().fsi_set_wait_limit(int(spins)), "fsi_set_wait_limit")
 
 
 def fsi_batched_lu_noalloc(A, npiv: int):
@@ -301,8 +306,10 @@ def rom_project(model: DeviceModel, V, F, rcv) -> DeviceROM:
     return DeviceROM(KR=KR.t(), DR=DR.t(), MR=MR.t(), fR=fR.t(), CR=CR.t())
 
 
-def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256):
-    """Reduced sweep: receiver pressures [nf][nrcv][nrhs] and SPL (torch, device)."""
+def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256, precision: str = "fp64", return_fp64: bool = False):
+    """Reduced sweep: receiver pressures [nf][nrcv][nrhs] and SPL (torch, device).  precision
+    "fp32_ir" (k <= 128) refines FP32 LUs against the FP64 residual; with return_fp64 the
+    per-frequency flags of FP64 re-solves are returned as well."""
     torch = _torch()
     lib = L.load()
     f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
@@ -313,14 +320,18 @@ def rom_sweep(rom: DeviceROM, freqs_hz, batch: int = 256):
     cm = lambda X: X.t().contiguous()   # column-major buffers
     KR, DR, MR, fR, CR = cm(rom.KR), cm(rom.DR), cm(rom.MR), cm(rom.fR), cm(rom.CR)
     bt = min(batch, nf)
+    prec = PRECISIONS[precision]
     need = C.c_size_t()
-    L.check(lib.rom_sweep_workspace(k, nrhs, nrcv, bt, C.byref(need)), "rom_sweep_workspace")
+    L.check(lib.rom_sweep_workspace(k, nrhs, nrcv, bt, prec, C.byref(need)), "rom_sweep_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
     p = torch.empty((nf, nrcv, nrhs), dtype=torch.complex128, device="cuda")
     spl = torch.empty((nf, nrcv, nrhs), dtype=torch.float64, device="cuda")
+    fb = np.zeros(nf, np.int32)
     L.check(lib.rom_sweep(k, _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR), nrhs, nrcv,
-                          f.ctypes.data_as(L.c_double_p), nf, bt, _ptr(ws), C.c_size_t(need.value), _ptr(p),
-                          _ptr(spl), _stream_ptr()), "rom_sweep")
+                          f.ctypes.data_as(L.c_double_p), nf, bt, prec, _ptr(ws), C.c_size_t(need.value), _ptr(p),
+                          _ptr(spl), fb.ctypes.data_as(L.c_int32_p), _stream_ptr()), "rom_sweep")
+    if return_fp64:
+        return p, spl, fb
     return p, spl
 
 
@@ -347,6 +358,98 @@ def rom_residual_check(model: DeviceModel, V, rom: DeviceROM, F, freqs_hz, batch
                                    C.c_size_t(need.value), out.ctypes.data_as(L.c_double_p), _stream_ptr()),
             "rom_residual_check")
     return out
+
+
+def rom_check_resolve(model: DeviceModel, V, rom: DeviceROM, F, rcv, freqs_hz, p, spl, res_tol: float,
+                      precision="fp32_ir", batch: int = 8, max_refine: int = 60, tol: float = 1e-10):
+    """Judge the reduced outputs p / spl ([nf][nrcv][nrhs] torch, device, updated in place) by the
+    full-order FP64 residual of the lifted reduced solutions; frequencies above res_tol are solved
+    again at full order and their outputs replace the reduced ones.  Returns (relres [nf][nrhs],
+    resolved [nf] 0/1, count)."""
+    torch = _torch()
+    lib = L.load()
+    f = np.ascontiguousarray(np.asarray(freqs_hz, dtype=np.float64))
+    nf = int(f.size)
+    k = rom.k
+    nrhs = int(F.shape[1])
+    cm = lambda X: X.t().contiguous()
+    KR, DR, MR, fR = cm(rom.KR), cm(rom.DR), cm(rom.MR), cm(rom.fR)
+    Vc, Fc = cm(V), cm(F)
+    r = rcv.to(torch.int32).contiguous()
+    nrcv = int(r.numel())
+    assert p.is_contiguous() and spl.is_contiguous() and p.shape == (nf, nrcv, nrhs)
+    bt = min(batch, nf)
+    o = _opts(precision, bt, max_refine, tol, False, refine="ir" if precision == "fp64" else "gmres")
+    need = C.c_size_t()
+    L.check(lib.rom_check_resolve_workspace(C.byref(model.dims), k, nrhs, nrcv, bt, C.byref(o), C.byref(need)),
+            "rom_check_resolve_workspace")
+    ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
+    rel = np.empty((nf, nrhs), np.float64)
+    res = np.zeros(nf, np.int32)
+    cnt = C.c_int(0)
+    L.check(lib.rom_check_resolve(C.byref(model.dims), _ptr(model.buf), _ptr(Vc), k, _ptr(KR), _ptr(DR), _ptr(MR),
+                                  _ptr(fR), _ptr(Fc), nrhs, _ptr(r), nrcv, f.ctypes.data_as(L.c_double_p), nf, bt,
+                                  float(res_tol), C.byref(o), _ptr(ws), C.c_size_t(need.value), _ptr(p), _ptr(spl),
+                                  rel.ctypes.data_as(L.c_double_p), res.ctypes.data_as(L.c_int32_p), C.byref(cnt),
+                                  _stream_ptr()), "rom_check_resolve")
+    return rel, res, cnt.value
+
+
+def rom_save(path: str, rom: DeviceROM, shifts_hz=(), V=None, band=(0.0, 0.0)):
+    """Write one reduced model (with its expansion points and, optionally, its basis V) to path."""
+    lib = L.load()
+    k = rom.k
+    cm = lambda X: X.t().contiguous()
+    bufs = [cm(rom.KR), cm(rom.DR), cm(rom.MR), cm(rom.fR), cm(rom.CR)]
+    Vc = cm(V) if V is not None else None
+    sh = np.ascontiguousarray(np.asarray(shifts_hz, dtype=np.float64))
+    lo, hi = np.array([band[0]], np.float64), np.array([band[1]], np.float64)
+    kk, ns = np.array([k], np.int32), np.array([sh.size], np.int32)
+    st = L.fsi_rom_store()
+    st.info = L.fsi_rom_info(nwin=1, kmax=k, nrhs=int(rom.fR.shape[1]), nrcv=int(rom.CR.shape[0]),
+                             n=int(V.shape[0]) if V is not None else 0, nshift_total=int(sh.size))
+    st.on_device = 1
+    st.KR, st.DR, st.MR, st.fR, st.CR = [_ptr(b) for b in bufs]
+    st.V = _ptr(Vc) if Vc is not None else None
+    st.lo, st.hi = lo.ctypes.data_as(L.c_double_p), hi.ctypes.data_as(L.c_double_p)
+    st.k, st.nshift = kk.ctypes.data_as(L.c_int32_p), ns.ctypes.data_as(L.c_int32_p)
+    st.shifts_hz = sh.ctypes.data_as(L.c_double_p) if sh.size else None
+    L.check(lib.rom_save(path.encode(), C.byref(st), _stream_ptr()), "rom_save")
+
+
+def rom_file_info(path: str) -> L.fsi_rom_info:
+    info = L.fsi_rom_info()
+    L.check(L.load().rom_file_info(path.encode(), C.byref(info)), "rom_file_info")
+    return info
+
+
+def rom_load(path: str):
+    """Read a one-window reduced model saved by rom_save: (DeviceROM, shifts_hz, V or None, band)."""
+    torch = _torch()
+    lib = L.load()
+    info = rom_file_info(path)
+    if info.nwin != 1:
+        raise ValueError("rom_load reads one-window files; this one has %d windows" % info.nwin)
+    k, nrhs, nrcv, n = info.kmax, info.nrhs, info.nrcv, int(info.n)
+    dev = dict(dtype=torch.complex128, device="cuda")
+    KR, DR, MR = (torch.empty((k, k), **dev) for _ in range(3))
+    fR = torch.empty((nrhs, k), **dev)
+    CR = torch.empty((k, nrcv), **dev)
+    V = torch.empty((k, n), **dev) if n > 0 else None
+    sh = np.zeros(max(info.nshift_total, 1), np.float64)
+    lo, hi = np.zeros(1), np.zeros(1)
+    kk, ns = np.zeros(1, np.int32), np.zeros(1, np.int32)
+    st = L.fsi_rom_store()
+    st.info = info
+    st.on_device = 1
+    st.KR, st.DR, st.MR, st.fR, st.CR = _ptr(KR), _ptr(DR), _ptr(MR), _ptr(fR), _ptr(CR)
+    st.V = _ptr(V) if V is not None else None
+    st.lo, st.hi = lo.ctypes.data_as(L.c_double_p), hi.ctypes.data_as(L.c_double_p)
+    st.k, st.nshift = kk.ctypes.data_as(L.c_int32_p), ns.ctypes.data_as(L.c_int32_p)
+    st.shifts_hz = sh.ctypes.data_as(L.c_double_p)
+    L.check(lib.rom_load(path.encode(), C.byref(st), _stream_ptr()), "rom_load")
+    rom = DeviceROM(KR=KR.t(), DR=DR.t(), MR=MR.t(), fR=fR.t(), CR=CR.t())
+    return rom, sh[:int(ns[0])].copy(), (V.t() if V is not None else None), (float(lo[0]), float(hi[0]))
 
 
 @dataclass

@@ -77,7 +77,7 @@ template <typename R>
 fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d_omega, cudaStream_t st) {
     const int b = m.b, nz = m.nz, ld = 3 * b;
     FSI_CUDA(cudaMemsetAsync(fc.status, 0, sizeof(int32_t) * F, st));
-    FSI_CUDA(cudaMemsetAsync(fc.tc_err, 0, sizeof(int32_t), st));
+    FSI_CUDA(cudaMemsetAsync(fc.tc.err, 0, sizeof(int32_t), st));
     launch_form_rows<R>(m, fc.G, fc.sG, ld, F, d_omega, 0, 0, 0, ld, st);
     FSI_CHECK_LAUNCH();
     for (int k = 0; k < nz; ++k) {
@@ -85,7 +85,7 @@ fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d
         const int ncols = std::min(3, nz - k) * b;
         if (k + 1 < nz) launch_form_rows<R>(m, fc.G, fc.sG, ld, F, d_omega, k + 1, b, k, ld, st);
         partial_lu<R>(fc.G, fc.sG, ld, F, m_rows, ncols, b, fc.ipiv + int64_t(k) * b, fc.sP, fc.status, st,
-                      fc.use_tc ? fc.tc_err : nullptr);
+                      fc.use_tc ? &fc.tc : nullptr);
         launch_slab_shift<R>(fc.G, fc.sG, F, b, m_rows, fc.U + int64_t(k) * b * 3 * b, fc.sU,
                              fc.L + int64_t(k) * b * b, fc.sL, fc.ipiv + int64_t(k) * b, fc.sP,
                              fc.perm + int64_t(k) * 2 * b, fc.sPerm, st);
@@ -131,8 +131,9 @@ struct SweepWS {
     size_t gws_bytes = 0;
     int64_t sV = 0;
 
-    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int gmres_restart) {
-        fc.carve(c, d, F, nrhs);
+    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int gmres_restart,
+               bool tensor) {
+        fc.carve(c, d, F, nrhs, tensor);
         sV = int64_t(nrhs) * d.n;
         omega = c.take<double>(F);
         xhat = c.take<double2>(size_t(F) * sV);
@@ -166,10 +167,10 @@ fsi_status check_dims(const fsi_dims* d) {
 }
 
 template <typename R>
-size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int restart) {
+size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int restart, bool tensor) {
     Carver c(nullptr, 0);
     SweepWS<R> w;
-    w.carve(c, d, F, nrhs, nrcv, host_io, restart);
+    w.carve(c, d, F, nrhs, nrcv, host_io, restart, tensor);
     return align_up(c.used);
 }
 
@@ -230,7 +231,7 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     Carver c(ws, ws_bytes);
     SweepWS<R> w;
     const int restart = gmres_restart_of(o);
-    w.carve(c, d, Fb_max, nrhs, nrcv, host_io, restart);
+    w.carve(c, d, Fb_max, nrhs, nrcv, host_io, restart, o.precision == FSI_TF32X3_IR);
     if (!c.fits()) {
         set_error("workspace too small: need " + std::to_string(align_up(c.used)) + " bytes");
         return FSI_ENOMEM;
@@ -269,7 +270,7 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         if (s != FSI_OK) return s;
         FSI_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
         int32_t htc = 0;
-        FSI_CUDA(cudaMemcpyAsync(&htc, w.fc.tc_err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        FSI_CUDA(cudaMemcpyAsync(&htc, w.fc.tc.err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         double2* pdst = host_io ? w.pb : reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs;
         double* sdst = host_io ? w.splb : (spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr);
         launch_receivers(m, w.omega, Fb, w.xhat, w.sV, rcvdev, nrcv, nrhs, pdst, sdst, st);
@@ -284,7 +285,7 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
         FSI_CUDA(cudaStreamSynchronize(st));
         prof().collect();
         if (htc) {
-            set_error("a tensor-core update gave up waiting for its MMAs");
+            set_error("a tensor-core update gave up waiting for its loads or MMAs");
             return FSI_ETIMEOUT;
         }
         for (int f = 0; f < Fb; ++f) {
@@ -300,7 +301,8 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     }
     S.launches = prof().launches;
     static_assert(int(PK_COUNT) == int(FSI_K_COUNT) && int(FSI_K_COUNT) <= int(FSI_K_SLOTS) &&
-                      int(PK_GEMV) == int(FSI_K_GEMV) && int(PK_SOLVE) == int(FSI_K_SOLVE),
+                      int(PK_GEMV) == int(FSI_K_GEMV) && int(PK_SOLVE) == int(FSI_K_SOLVE) &&
+                      int(PK_PACK) == int(FSI_K_PACK) && int(PK_TCGEMM) == int(FSI_K_TCGEMM),
                   "kernel classes of the profiler and the C ABI differ");
     for (int i = 0; i < PK_COUNT; ++i) {
         S.kernel_ms[i] = prof().ms[i];
@@ -420,8 +422,9 @@ fsi_status frf_sweep_workspace(const fsi_dims* dims, const fsi_solve_opts* opts,
     FSI_REQUIRE(opts && bytes && nrhs > 0 && nrcv > 0 && opts->batch > 0, "bad sweep workspace arguments");
     const bool hio = opts->host_io != 0;
     const int rs = gmres_restart_of(*opts);
-    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio, rs)
-                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio, rs);
+    const bool tc = opts->precision == FSI_TF32X3_IR;
+    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio, rs, false)
+                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio, rs, tc);
     return FSI_OK;
 }
 
@@ -463,9 +466,14 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
     return FSI_OK;
 }
 
-fsi_status fsi_lu_workspace(int batch, int m, size_t* bytes) {
-    FSI_REQUIRE(batch > 0 && m > 0 && bytes, "bad lu workspace arguments");
-    *bytes = align_up(sizeof(int32_t) * size_t(batch + 1));
+fsi_status fsi_lu_workspace(int precision, int batch, int m, int ncols, int npiv, size_t* bytes) {
+    FSI_REQUIRE(batch > 0 && m > 0 && ncols > 0 && npiv > 0 && npiv <= m && npiv <= ncols && bytes,
+                "bad lu workspace arguments");
+    FSI_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR || precision == FSI_TF32X3_IR,
+                "unknown precision");
+    size_t b = align_up(sizeof(int32_t) * size_t(batch + 1));
+    if (precision == FSI_TF32X3_IR) b += align_up(tc_workspace_bytes(batch, m, ncols, npiv));
+    *bytes = b;
     return FSI_OK;
 }
 
@@ -473,16 +481,29 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
                           int32_t* ipiv, void* ws, size_t ws_bytes, int* n_singular_out, void* stream) {
     FSI_REQUIRE(A && ipiv && ws && batch > 0 && m > 0 && ncols > 0, "bad batched lu arguments");
     FSI_REQUIRE(npiv > 0 && npiv <= m && npiv <= ncols && ld >= ncols && sA >= ld * m, "bad batched lu shape");
-    FSI_REQUIRE(ws_bytes >= sizeof(int32_t) * size_t(batch + 1), "workspace too small");
+    FSI_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR || precision == FSI_TF32X3_IR,
+                "unknown precision");
+    size_t need = 0;
+    fsi_status s0 = fsi_lu_workspace(precision, batch, m, ncols, npiv, &need);
+    if (s0 != FSI_OK) return s0;
+    FSI_REQUIRE(ws_bytes >= need, "workspace too small");
     FSI_REQUIRE(m <= 8192, "m too large for the panel kernel");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int32_t* status = static_cast<int32_t*>(ws);
     FSI_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t) * (batch + 1), st));
-    if (precision == FSI_FP64)
+    if (precision == FSI_FP64) {
         partial_lu<double>(static_cast<double2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st);
-    else
+    } else {
+        TcCtx tc;
+        if (precision == FSI_TF32X3_IR) {
+            const size_t off = align_up(sizeof(int32_t) * size_t(batch + 1));
+            tc.err = status + batch;
+            tc.ws = static_cast<char*>(ws) + off;
+            tc.ws_bytes = ws_bytes - off;
+        }
         partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st,
-                          precision == FSI_TF32X3_IR ? status + batch : nullptr);
+                          precision == FSI_TF32X3_IR ? &tc : nullptr);
+    }
     FSI_CHECK_LAUNCH();
     if (n_singular_out || precision == FSI_TF32X3_IR) {
         std::vector<int32_t> h(batch + 1);
@@ -492,10 +513,16 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
         for (int i = 0; i < batch; ++i) cnt += h[i] != 0;
         if (n_singular_out) *n_singular_out = cnt;
         if (precision == FSI_TF32X3_IR && h[batch]) {
-            set_error("a tensor-core update gave up waiting for its MMAs");
+            set_error("a tensor-core update gave up waiting for its loads or MMAs");
             return FSI_ETIMEOUT;
         }
     }
+    return FSI_OK;
+}
+
+fsi_status fsi_set_wait_limit(int64_t spins) {
+    FSI_REQUIRE(spins >= 0, "spin limit must be >= 0");
+    set_tc_spin_limit(spins > int64_t(UINT32_MAX) ? UINT32_MAX : uint32_t(spins));
     return FSI_OK;
 }
 

@@ -21,11 +21,11 @@ struct Factor {
     int32_t* ipiv = nullptr;
     int32_t* perm = nullptr;
     int32_t* status = nullptr;
-    int32_t* tc_err = nullptr;   // set: trailing updates on the tensor cores (FP32 storage only)
+    TcCtx tc;                    // tensor-core updates (FP32 storage only): error flag, operand packs
     bool use_tc = false;
     int64_t sG = 0, sU = 0, sL = 0, sP = 0, sPerm = 0;
 
-    void carve(Carver& c, const fsi_dims& d, int F, int nrhs) {
+    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, bool tensor = false) {
         const int64_t b = d.b, nz = d.nz;
         sG = 2 * b * 3 * b;
         sU = nz * b * 3 * b;
@@ -38,7 +38,11 @@ struct Factor {
         ipiv = c.take<int32_t>(size_t(F) * sP);
         perm = c.take<int32_t>(size_t(F) * sPerm);
         status = c.take<int32_t>(size_t(F));
-        tc_err = c.take<int32_t>(1);
+        tc.err = c.take<int32_t>(1);
+        if (tensor && sizeof(R) == 4) {
+            tc.ws_bytes = tc_workspace_bytes(F, 2 * d.b, 3 * d.b, d.b);
+            tc.ws = c.take<char>(tc.ws_bytes);
+        }
     }
 };
 

@@ -129,18 +129,30 @@ template <typename R>
 void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1,
                         int k0, int K, cudaStream_t st);
 
-// Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (3xTF32); err gets 1 if a
-// bounded wait gave up.
-void launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
-                      int32_t* err, cudaStream_t st);
+// Tensor-core trailing updates: device error flag (set to 1 when a bounded wait gave up) and the
+// workspace that holds the split operands of one update.
+struct TcCtx {
+    int32_t* err = nullptr;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+};
+// Workspace bytes for every trailing update of partial_lu(F, m, ncols, npiv) on the tensor cores.
+size_t tc_workspace_bytes(int F, int m, int ncols, int npiv);
+// Spin limit of the tensor-core kernels' pipeline waits (0: the default, about 6.7e7 polls).
+void set_tc_spin_limit(uint32_t spins);
+// Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (3xTF32, TMA-fed).
+// Returns false (nothing launched) when the operands do not meet TMA's alignment rules or the
+// workspace is too small; the caller then runs the SIMT update.
+bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
+                      const TcCtx& tc, cudaStream_t st);
 
-// Batched partial LU driver on device matrices (uses the kernels above).  With tc_err != NULL
-// (FP32 only) the outer trailing updates run on the tensor cores.
+// Batched partial LU driver on device matrices (uses the kernels above).  With tc != NULL
+// (FP32 only) the large trailing updates run on the tensor cores.
 template <typename R>
 int panel_width(int m);
 template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv,
-                int32_t* ipiv, int64_t sP, int32_t* status, cudaStream_t st, int32_t* tc_err = nullptr);
+                int32_t* ipiv, int64_t sP, int32_t* status, cudaStream_t st, const TcCtx* tc = nullptr);
 
 // After a slab step: save factor rows and multipliers, turn ipiv into a row
 // permutation of the stacked rows, and move the Schur tail to the top rows.

@@ -522,19 +522,27 @@ void launch_gemm_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r
 
 template <typename R>
 void trailing_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
-                     int32_t* tc_err, cudaStream_t st) {
+                     const TcCtx* tc, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (tc_err) {
-            launch_tc_update(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc_err, st);
-            return;
-        }
+        if (tc && launch_tc_update(G, sG, ld, F, r0, r1, c0, c1, k0, K, *tc, st)) return;
     }
     launch_gemm_update<R>(G, sG, ld, F, r0, r1, c0, c1, k0, K, st);
 }
 
+// rows per block of the left-looking solve U12 = L11^-1 A12 of the columns right of the pivots
+constexpr int kLazyTrsmRows = 128;
+
+// Partial LU of the first npiv columns, right-looking in outer panels of NB columns, with the
+// updates of the outer panels restricted to the pivot columns [0, npiv).  The columns right of
+// them, [npiv, ncols), only receive their row interchanges while the pivot columns are
+// factored; afterwards U12 = L11^-1 A12 is solved left-looking in 128-row blocks (each block
+// first takes the product of the multipliers and all rows above it, K up to npiv) and the
+// Schur complement A22 -= L21 U12 is one update with K = npiv.  The arithmetic is that of the
+// right-looking order (the same pivots; sums in a different order), but most of it runs in
+// updates with a long K.
 template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv, int32_t* ipiv,
-                int64_t sP, int32_t* status, cudaStream_t st, int32_t* tc_err) {
+                int64_t sP, int32_t* status, cudaStream_t st, const TcCtx* tc) {
     const int NB = outer_nb<R>();
     const int nbw = std::min(panel_width<R>(m), NB);
     for (int J = 0; J < npiv; J += NB) {
@@ -549,10 +557,18 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
             }
         }
         launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);
-        if (J + nb < ncols) {
-            blocked_trsm<R>(G, sG, ld, F, J, nb, J + nb, ncols, st);
-            trailing_update<R>(G, sG, ld, F, J + nb, m, J + nb, ncols, J, nb, tc_err, st);
+        if (J + nb < npiv) {
+            blocked_trsm<R>(G, sG, ld, F, J, nb, J + nb, npiv, st);
+            trailing_update<R>(G, sG, ld, F, J + nb, m, J + nb, npiv, J, nb, tc, st);
         }
+    }
+    if (npiv < ncols) {
+        for (int I = 0; I < npiv; I += kLazyTrsmRows) {
+            const int tb = std::min(kLazyTrsmRows, npiv - I);
+            if (I > 0) trailing_update<R>(G, sG, ld, F, I, I + tb, npiv, ncols, 0, I, tc, st);
+            blocked_trsm<R>(G, sG, ld, F, I, tb, npiv, ncols, st);
+        }
+        if (npiv < m) trailing_update<R>(G, sG, ld, F, npiv, m, npiv, ncols, 0, npiv, tc, st);
     }
 }
 
@@ -594,7 +610,7 @@ void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, in
     template void launch_trsm<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, cudaStream_t);                 \
     template void launch_gemm_update<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, int, int, cudaStream_t); \
     template void partial_lu<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*,         \
-                                cudaStream_t, int32_t*);                                                             \
+                                cudaStream_t, const TcCtx*);                                                         \
     template void launch_slab_shift<R>(Cplx<R>::T*, int64_t, int, int, int, Cplx<R>::T*, int64_t, Cplx<R>::T*,      \
                                        int64_t, const int32_t*, int64_t, int32_t*, int64_t, cudaStream_t);           \
     template void launch_backsub<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, cudaStream_t);

@@ -11,8 +11,8 @@
 // the library holds that array (16 KiB) until the process exits.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <sstream>
+#include <string>
 
 #include "fsi_internal.h"
 #include "kernels.cuh"
@@ -22,14 +22,9 @@ namespace fsi {
 namespace {
 
 constexpr int kNoAllocMaxBatch = 4095;   // matrices per call; one more slot holds the counter
-constexpr int kMaxDevices = 64;
 
 // Status flags [0, batch) and the singular-matrix counter [kNoAllocMaxBatch].
 static __device__ __align__(256) int32_t g_lu_scratch[kNoAllocMaxBatch + 1];
-
-// Device addresses of g_lu_scratch, looked up once per device.
-std::mutex g_mu;
-int32_t* g_scratch_addr[kMaxDevices] = {nullptr};
 
 __global__ void count_flags_kernel(const int32_t* flags, int batch, int32_t* counter) {
     int c = 0;
@@ -38,28 +33,17 @@ __global__ void count_flags_kernel(const int32_t* flags, int batch, int32_t* cou
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(counter, c);
 }
 
+// Device address of g_lu_scratch for the current device.  Looked up on every call: the lookup
+// is host-side and cheap, and a cached address would dangle after the context is torn down and
+// recreated (the module, and with it the array, may then load elsewhere).
 fsi_status scratch_for_current_device(int32_t** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_lu_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error(std::string("cudaGetSymbolAddress(g_lu_scratch): ") + cudaGetErrorString(e));
         return FSI_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("device index out of range for the no-alloc scratch table");
-        return FSI_EINVAL;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_lu_scratch);   // this device is current
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("cudaGetSymbolAddress(g_lu_scratch): ") + cudaGetErrorString(e));
-            return FSI_ECUDA;
-        }
-        g_scratch_addr[dev] = static_cast<int32_t*>(p);
-    }
-    *out = g_scratch_addr[dev];
+    *out = static_cast<int32_t*>(p);
     return FSI_OK;
 }
 
@@ -78,6 +62,14 @@ extern "C" fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, in
     }
     if (!(npiv > 0 && npiv <= m && npiv <= ncols && ld >= ncols && sA >= ld * m)) {
         set_error("fsi_batched_lu_noalloc: bad shape");
+        return FSI_EINVAL;
+    }
+    if (precision == FSI_TF32X3_IR) {
+        set_error("fsi_batched_lu_noalloc: FSI_TF32X3_IR needs an operand workspace; use fsi_batched_lu");
+        return FSI_EINVAL;
+    }
+    if (precision != FSI_FP64 && precision != FSI_FP32_IR) {
+        set_error("fsi_batched_lu_noalloc: unknown precision");
         return FSI_EINVAL;
     }
     if (batch > kNoAllocMaxBatch) {
@@ -105,7 +97,8 @@ extern "C" fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, in
     if (precision == FSI_FP64)
         partial_lu<double>(static_cast<double2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, scratch, st);
     else
-        partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, scratch, st);
+        partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, scratch, st,
+                          nullptr);
     count_flags_kernel<<<1, 256, 0, st>>>(scratch, batch, scratch + kNoAllocMaxBatch);
     e = cudaGetLastError();
     if (e == cudaSuccess && n_singular_out) {

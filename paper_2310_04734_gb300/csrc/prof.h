@@ -8,7 +8,7 @@
 
 namespace fsi {
 
-enum ProfKind { PK_GEMM = 0, PK_PANEL, PK_TRSM, PK_LASWP, PK_FORM, PK_SHIFT, PK_SOLVE, PK_RESID, PK_GEMV, PK_COUNT };
+enum ProfKind { PK_GEMM = 0, PK_PANEL, PK_TRSM, PK_LASWP, PK_FORM, PK_SHIFT, PK_SOLVE, PK_RESID, PK_GEMV, PK_PACK, PK_TCGEMM, PK_COUNT };
 
 struct ProfRec {
     int kind;

@@ -626,7 +626,7 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                 axpby_kernel<<<cdiv(n, 256), 256, 0, st>>>(make_double2(1.0 / nu, 0), w.W, make_double2(0, 0),
                                                           nullptr, w.Qs, n);
                 ROM_CUDA(cudaMemsetAsync(w.Ps, 0, sizeof(double2) * n, st));
-                int nq = 1;
+                int nq = 1, ndefl = 0;
                 for (int j = 0; j + 1 < q; ++j) {
                     // B = Dt q_j + M p_j ; r = -Kt^-1 B
                     spmv_kernel<<<dim3(spmv_grid_x(n, 1), 1), kRowThreads, 0, st>>>(
@@ -650,12 +650,26 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                     s = sqnorm(w.W, n, w.cg.scal, t2, st);
                     if (s != FSI_OK) return s;
                     const double t = std::sqrt(t2);
-                    if (!(t > kDeflate * nu)) break;
-                    axpby_kernel<<<cdiv(n, 256), 256, 0, st>>>(make_double2(1.0 / t, 0), w.W, make_double2(0, 0),
-                                                              nullptr, w.Qs + int64_t(j + 1) * n, n);
-                    axpby_kernel<<<cdiv(n, 256), 256, 0, st>>>(make_double2(1.0 / t, 0), sv, make_double2(0, 0),
-                                                              nullptr, w.Ps + int64_t(j + 1) * n, n);
-                    ROM_LAUNCH();
+                    if (t > kDeflate * nu) {
+                        axpby_kernel<<<cdiv(n, 256), 256, 0, st>>>(make_double2(1.0 / t, 0), w.W,
+                                                                  make_double2(0, 0), nullptr,
+                                                                  w.Qs + int64_t(j + 1) * n, n);
+                        axpby_kernel<<<cdiv(n, 256), 256, 0, st>>>(make_double2(1.0 / t, 0), sv, make_double2(0, 0),
+                                                                  nullptr, w.Ps + int64_t(j + 1) * n, n);
+                        ROM_LAUNCH();
+                    } else {
+                        // deflation (Bai and Su): r is in the span already; continue with q = 0 and
+                        // p = s, which can still reach new directions, unless s vanishes
+                        // (breakdown).  A second deflation in one sequence stops it.
+                        double s2 = 0.0;
+                        s = sqnorm(sv, n, w.cg.scal, s2, st);
+                        if (s != FSI_OK) return s;
+                        if (ndefl > 0 || !(std::sqrt(s2) > kDeflate)) break;
+                        ++ndefl;
+                        ROM_CUDA(cudaMemsetAsync(w.Qs + int64_t(j + 1) * n, 0, sizeof(double2) * n, st));
+                        ROM_CUDA(cudaMemcpyAsync(w.Ps + int64_t(j + 1) * n, sv, sizeof(double2) * n,
+                                                 cudaMemcpyDeviceToDevice, st));
+                    }
                     ++nq;
                 }
                 if (keep) {
@@ -866,30 +880,110 @@ fsi_status rom_project(const fsi_dims* dims, const void* d_model, const fsi_c64*
     return FSI_OK;
 }
 
-fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, size_t* bytes) {
+// FP32_IR reduced sweep: chunk buffers of the persistent multi-model kernel (one model) and the
+// FP64 fallback for frequencies whose refinement stalls.
+struct Fp32SweepBufs {
+    fsi_rom_item* item;
+    int32_t* offs;
+    int* counter;
+    int32_t* status;
+    double* fdev;
+    void* fb_ws;
+    size_t fb_bytes;
+    void carve(Carver& c, int k, int nrhs, int batch) {
+        item = c.take<fsi_rom_item>(1);
+        offs = c.take<int32_t>(2);
+        counter = c.take<int>(1);
+        status = c.take<int32_t>(batch);
+        fdev = c.take<double>(batch);
+        fb_bytes = reduced_solve_ws(k, nrhs, 1);
+        fb_ws = c.take<char>(fb_bytes);
+    }
+};
+
+fsi_status rom_sweep_workspace(int k, int nrhs, int nrcv, int batch, int precision, size_t* bytes) {
     ROM_REQUIRE(k > 0 && nrhs > 0 && nrcv > 0 && batch > 0 && bytes, "bad rom sweep workspace arguments");
-    *bytes = reduced_solve_ws(k, nrhs, batch);
+    ROM_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR, "unknown precision");
+    if (precision == FSI_FP64) {
+        *bytes = reduced_solve_ws(k, nrhs, batch);
+    } else {
+        Carver c(nullptr, 0);
+        Fp32SweepBufs b;
+        b.carve(c, k, nrhs, batch);
+        *bytes = align_up(c.used);
+    }
     return FSI_OK;
 }
 
 fsi_status rom_sweep(int k, const fsi_c64* KR, const fsi_c64* DR, const fsi_c64* MR, const fsi_c64* fR,
-                     const fsi_c64* CR, int nrhs, int nrcv, const double* f_hz, int nf, int batch, void* ws,
-                     size_t ws_bytes, fsi_c64* p_out, double* spl_out, void* stream) {
+                     const fsi_c64* CR, int nrhs, int nrcv, const double* f_hz, int nf, int batch, int precision,
+                     void* ws, size_t ws_bytes, fsi_c64* p_out, double* spl_out, int32_t* fp64_out, void* stream) {
     ROM_REQUIRE(KR && DR && MR && fR && CR && f_hz && ws && p_out, "NULL argument");
     ROM_REQUIRE(k > 0 && k <= 8192 && nrhs > 0 && nrcv > 0 && nf > 0 && batch > 0, "bad rom sweep sizes");
+    ROM_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR, "unknown precision");
+    ROM_REQUIRE(precision == FSI_FP64 || (k <= 128 && nrhs <= 4),
+                "FSI_FP32_IR reduced sweep needs k <= 128 and nrhs <= 4 (use FSI_FP64)");
     const int bt = std::min(batch, nf);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const double2 *K2 = reinterpret_cast<const double2*>(KR), *D2 = reinterpret_cast<const double2*>(DR),
+                  *M2 = reinterpret_cast<const double2*>(MR), *f2 = reinterpret_cast<const double2*>(fR),
+                  *C2 = reinterpret_cast<const double2*>(CR);
+    if (fp64_out) std::fill(fp64_out, fp64_out + nf, 0);
+    if (precision == FSI_FP64) {
+        for (int f0 = 0; f0 < nf; f0 += bt) {
+            const int Fb = std::min(bt, nf - f0);
+            ReducedBatch rb;
+            fsi_status s = reduced_solve_batch(k, K2, D2, M2, f2, nrhs, f_hz + f0, Fb, ws, ws_bytes, rb, st);
+            if (s != FSI_OK) return s;
+            s = reduced_receivers(rb, C2, nrcv, reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs,
+                                  spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr, st);
+            if (s != FSI_OK) return s;
+        }
+        ROM_CUDA(cudaStreamSynchronize(st));
+        return FSI_OK;
+    }
+    Carver c(ws, ws_bytes);
+    Fp32SweepBufs b;
+    b.carve(c, k, nrhs, bt);
+    if (!c.fits()) {
+        set_error("rom_sweep workspace too small");
+        return FSI_ENOMEM;
+    }
+    std::vector<int32_t> hs(bt);
     for (int f0 = 0; f0 < nf; f0 += bt) {
         const int Fb = std::min(bt, nf - f0);
-        ReducedBatch rb;
-        fsi_status s = reduced_solve_batch(k, reinterpret_cast<const double2*>(KR), reinterpret_cast<const double2*>(DR),
-                                           reinterpret_cast<const double2*>(MR), reinterpret_cast<const double2*>(fR),
-                                           nrhs, f_hz + f0, Fb, ws, ws_bytes, rb, st);
+        fsi_rom_item it{};
+        it.k = k;
+        it.nrhs = nrhs;
+        it.nrcv = nrcv;
+        it.nf = Fb;
+        it.KR = KR;
+        it.DR = DR;
+        it.MR = MR;
+        it.fR = fR;
+        it.CR = CR;
+        it.f_hz = b.fdev;
+        it.p_out = p_out + int64_t(f0) * nrcv * nrhs;
+        it.spl_out = spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr;
+        const int32_t offs[2] = {0, Fb};
+        ROM_CUDA(cudaMemcpyAsync(b.fdev, f_hz + f0, sizeof(double) * Fb, cudaMemcpyHostToDevice, st));
+        ROM_CUDA(cudaMemcpyAsync(b.item, &it, sizeof(it), cudaMemcpyHostToDevice, st));
+        ROM_CUDA(cudaMemcpyAsync(b.offs, offs, sizeof(offs), cudaMemcpyHostToDevice, st));
+        fsi_status s = rom_multi_sweep(b.item, 1, b.offs, Fb, b.counter, b.status, stream);
         if (s != FSI_OK) return s;
-        s = reduced_receivers(rb, reinterpret_cast<const double2*>(CR), nrcv,
-                              reinterpret_cast<double2*>(p_out) + int64_t(f0) * nrcv * nrhs,
-                              spl_out ? spl_out + int64_t(f0) * nrcv * nrhs : nullptr, st);
-        if (s != FSI_OK) return s;
+        ROM_CUDA(cudaMemcpyAsync(hs.data(), b.status, sizeof(int32_t) * Fb, cudaMemcpyDeviceToHost, st));
+        ROM_CUDA(cudaStreamSynchronize(st));   // the host item above stays alive until here
+        for (int i = 0; i < Fb; ++i) {
+            if (hs[i] == 0) continue;
+            // refinement stalled (or a zero FP32 pivot): this frequency again by the FP64 LU
+            ReducedBatch rb;
+            s = reduced_solve_batch(k, K2, D2, M2, f2, nrhs, f_hz + f0 + i, 1, b.fb_ws, b.fb_bytes, rb, st);
+            if (s != FSI_OK) return s;
+            s = reduced_receivers(rb, C2, nrcv, reinterpret_cast<double2*>(p_out) + int64_t(f0 + i) * nrcv * nrhs,
+                                  spl_out ? spl_out + int64_t(f0 + i) * nrcv * nrhs : nullptr, st);
+            if (s != FSI_OK) return s;
+            if (fp64_out) fp64_out[f0 + i] = 1;
+        }
     }
     ROM_CUDA(cudaStreamSynchronize(st));
     return FSI_OK;

@@ -1,4 +1,5 @@
-// Trailing update of the band LU on the 5th-generation tensor cores (tcgen05).
+// Trailing updates of the band LU on the 5th-generation tensor cores (tcgen05),
+// with operands and results moved by the Tensor Memory Accelerator (TMA).
 //
 //   C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] * B[k0:k0+K, c0:c1]      (complex FP32, row major)
 //
@@ -7,26 +8,36 @@
 // [[Br, Bi], [-Bi, Br]], C' -= A' B' is exactly the complex update on the
 // interleaved C.  FP32 accuracy is kept on the TF32 tensor pipe by splitting
 // every operand into hi = tf32(x) and lo = tf32(x - hi) and accumulating
-// hi*hi + hi*lo + lo*hi in FP32.  Plain TF32 products are not accurate enough
-// for the refinement of these systems to converge.  hi*hi and the two cross
+// hi*hi + hi*lo + lo*hi in FP32 (plain TF32 products are not accurate enough
+// for the refinement of these systems to converge).  hi*hi and the two cross
 // terms accumulate in separate TMEM accumulators, added in FP32 only in the
-// epilogue: the tensor core aligns products to the accumulator's exponent and
-// truncates, which would drop most of the small cross terms if they were added
-// into the large hi*hi sum.
+// epilogue, so the small cross terms are not aligned to the large hi*hi sum.
 //
-// One CTA (8 warps) per 128 x 256 real tile.  For each 32-float K slice the
-// threads load A' and B' from global memory (vector loads), split them and
-// store whole 16-byte chunks into shared memory in the 128-byte-swizzled
-// K-major layout the MMA descriptors describe; two slice buffers alternate and
-// the next slice is prefetched into registers while the current slice's MMAs
-// run.  One thread issues tcgen05.mma (M=128, N=256, K=8, kind::tf32) and
-// commits to an mbarrier per buffer.  The epilogue reads both accumulators with
-// tcgen05.ld, stages them through shared memory and subtracts them from C with
-// coalesced row accesses.  Every mbarrier wait is bounded: on timeout the CTA
-// records an error, stops issuing work, and still frees its tensor memory.
+// Two kernels per update:
+//   pack:  A' and B' are split into hi/lo planes in K-major layout (rows of
+//          Kp floats, Kp = 2K rounded up to 32, zero padded): A' rows are the
+//          rows of C, B' rows are the real columns of C (B transposed).
+//   gemm:  one CTA per 128 x 256 real tile of C and frequency, warp
+//          specialised: warp 0 issues the TMA loads of the four operand tiles
+//          of a 32-float K slice into a two-stage ring (128-byte swizzle),
+//          warp 1 issues the tcgen05.mma instructions (M=128, N=256, K=8,
+//          kind::tf32; 12 per slice) and commits them to the stage's "empty"
+//          mbarrier, and warps 4..7 read both accumulators with tcgen05.ld,
+//          stage -(hh + cross) in swizzled shared memory and add it into C
+//          with TMA bulk reductions (cp.reduce.async.bulk.tensor .add), which
+//          also drop the rows and columns outside C.
+// Every mbarrier wait is bounded by a spin limit (a kernel argument): on a
+// timeout the CTA records an error, stops issuing work, waits (with a fixed
+// generous limit) for the TMA loads and MMAs it already issued, and only then
+// frees its tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
+#include <algorithm>
+#include <mutex>
 
 #include "kernels.cuh"
 #include "prof.h"
@@ -35,23 +46,20 @@ namespace fsi {
 
 namespace {
 
-constexpr int kTM = 128;            // real rows per tile (MMA M)
-constexpr int kTN = 256;            // real columns per tile (MMA N)
-constexpr int kTK = 32;             // real K per shared-memory slice (one 128-byte swizzle row)
+constexpr int kTM = 128;             // real rows per tile (MMA M)
+constexpr int kTN = 256;             // real columns per tile (MMA N)
+constexpr int kTKf = 32;             // floats per K slice: one 128-byte swizzle row
 constexpr int kThreads = 256;
-constexpr int kTmemCols = 512;      // two 256-column fp32 accumulators: hi*hi, and hi*lo + lo*hi
-constexpr uint32_t kSpinLimit = 1u << 26;
-
-// shared memory: per stage A_hi, A_lo (kTM x 128 B), B_hi, B_lo (kTN x 128 B)
-constexpr int kABytes = kTM * 128;
-constexpr int kBBytes = kTN * 128;
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // 96 KiB
+constexpr int kTmemCols = 512;       // two 256-column fp32 accumulators: hi*hi, and hi*lo + lo*hi
 constexpr int kStages = 2;
-constexpr size_t kSmemBytes = size_t(kStages) * kStageBytes + 1024 + 64;
+constexpr int kABytes = kTM * 128;   // one plane of an A slice
+constexpr int kBBytes = kTN * 128;   // one plane of a B slice
+constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // 96 KiB
+constexpr size_t kSmemBytes = size_t(kStages) * kStageBytes + 1024 + 128;
+constexpr uint32_t kDefaultSpin = 1u << 26;
+constexpr uint32_t kDrainSpin = 1u << 26;   // waits for work already issued (always completes)
 
-// per-thread items of one slice: A' 128 rows x 8 chunks, B 128 complex columns x 8 chunks
-constexpr int kAItems = (kTM * (kTK / 4)) / kThreads;            // 4
-constexpr int kBItems = ((kTN / 2) * (kTK / 4)) / kThreads;      // 4
+std::atomic<uint32_t> g_spin_limit{kDefaultSpin};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -63,23 +71,68 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-// byte offset of the 16-byte chunk c (k = 4c..4c+3) of row `row` of a K-major tile with
-// 128-byte rows in the 128-byte swizzle: chunk index XOR (row mod 8), 8-row groups of 1024 B
-__device__ __forceinline__ uint32_t sw128_chunk(int row, int c) {
-    return uint32_t(row) * 128u + (uint32_t(c ^ (row & 7)) << 4);
+// ----------------------------------------------------------------- operand packing
+// Ap[2f + plane][r][kk] = split(A'[r0 + r][2 k0 + kk]) for kk < 2K, 0 up to Kp.
+__global__ void pack_a_kernel(const float* __restrict__ G, int64_t sGf, int64_t ldf, int r0, int M, int kx0, int K2,
+                              int Kp, float* __restrict__ Ap) {
+    const int f = blockIdx.y;
+    const int64_t idx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    const int64_t plane = int64_t(M) * Kp;
+    if (idx >= plane) return;
+    const int r = int(idx / Kp), kk = int(idx - int64_t(r) * Kp);
+    const float* src = G + f * sGf + int64_t(r0 + r) * ldf + kx0;
+    float v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = (kk + j < K2) ? src[kk + j] : 0.f;
+    float4 hi, lo;
+    hi.x = to_tf32(v[0]); lo.x = to_tf32(v[0] - hi.x);
+    hi.y = to_tf32(v[1]); lo.y = to_tf32(v[1] - hi.y);
+    hi.z = to_tf32(v[2]); lo.z = to_tf32(v[2] - hi.z);
+    hi.w = to_tf32(v[3]); lo.w = to_tf32(v[3] - hi.w);
+    float* dst = Ap + int64_t(2 * f) * plane + idx;
+    *reinterpret_cast<float4*>(dst) = hi;
+    *reinterpret_cast<float4*>(dst + plane) = lo;
 }
 
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, float a, float b, float c, float d) {
-    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+// Bp[2f + plane][q][kk]: row q = 2n holds (Br, -Bi) and row 2n + 1 holds (Bi, Br) of every
+// complex k (at kk = 2k, 2k + 1), zero for k >= K; B[k][n] = G[k0 + k][c0 + n].
+__global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, int k0, int K, int c0, int N, int Kp,
+                              float* __restrict__ Bp) {
+    __shared__ float2 t[32][33];
+    const int f = blockIdx.z;
+    const int kb = blockIdx.x * 32, nb = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const float2* Gf = G + f * sG;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int k = kb + ty + 8 * i, n = nb + tx;
+        t[ty + 8 * i][tx] = (k < K && n < N) ? Gf[int64_t(k0 + k) * ld + c0 + n] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    const int64_t plane = int64_t(2 * N) * Kp;
+    float* hiP = Bp + int64_t(2 * f) * plane;
+    float* loP = hiP + plane;
+    const int k = kb + tx;
+    if (2 * k >= Kp) return;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int nl = ty + 8 * i, n = nb + nl;
+        if (n >= N) continue;
+        const float2 b = t[tx][nl];
+        const int64_t o0 = int64_t(2 * n) * Kp + 2 * k, o1 = o0 + Kp;
+        float2 h0, l0, h1, l1;
+        h0.x = to_tf32(b.x);  l0.x = to_tf32(b.x - h0.x);
+        h0.y = to_tf32(-b.y); l0.y = to_tf32(-b.y - h0.y);
+        h1.x = to_tf32(b.y);  l1.x = to_tf32(b.y - h1.x);
+        h1.y = h0.x;          l1.y = l0.x;
+        *reinterpret_cast<float2*>(hiP + o0) = h0;
+        *reinterpret_cast<float2*>(loP + o0) = l0;
+        *reinterpret_cast<float2*>(hiP + o1) = h1;
+        *reinterpret_cast<float2*>(loP + o1) = l1;
+    }
 }
 
-// hi / lo split of four values written as two 16-byte chunks
-__device__ __forceinline__ void put_split(uint32_t hi_addr, uint32_t lo_addr, float4 v) {
-    const float h0 = to_tf32(v.x), h1 = to_tf32(v.y), h2 = to_tf32(v.z), h3 = to_tf32(v.w);
-    st_shared_v4(hi_addr, h0, h1, h2, h3);
-    st_shared_v4(lo_addr, to_tf32(v.x - h0), to_tf32(v.y - h1), to_tf32(v.z - h2), to_tf32(v.w - h3));
-}
-
+// ----------------------------------------------------------------- tcgen05 / TMA helpers
 // shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 bytes apart
 __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     uint64_t d = 0;
@@ -105,18 +158,38 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
                  : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32_t limit) {
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}\n"
             : "=r"(done)
-            : "r"(mbar), "r"(phase)
+            : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void tma_load3(uint32_t dst, const CUtensorMap* map, int x, int y, int z, uint32_t mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(mbar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_reduce_add3(const CUtensorMap* map, int x, int y, int z, uint32_t src) {
+    asm volatile(
+        "cp.reduce.async.bulk.tensor.3d.global.shared::cta.add.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(x), "r"(y), "r"(z), "r"(src)
+        : "memory");
 }
 
 // 32 consecutive fp32 columns of this warp's 32 TMEM lanes (one register per column)
@@ -131,38 +204,45 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
         : "r"(taddr));
 }
 
-struct SliceRegs {
-    float4 a[kAItems];
-    float2 b0[kBItems], b1[kBItems];
+struct TcArgs {
+    int cx0, cx1;     // real columns [2 c0, 2 c1) of C
+    int cy0, cy1;     // rows [r0, r1) of C
+    int nk;           // K slices of kTKf floats
+    uint32_t limit;   // spin limit of the pipeline waits
+    int32_t* err;
 };
 
-__global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(float2* G, int64_t sG, int ld, int r0, int r1, int c0,
-                                                                int c1, int k0, int K, int32_t* err) {
+__global__ void __launch_bounds__(kThreads, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, TcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char* ops = smem_raw + pad;
     const uint32_t ops_s = raw + pad;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(ops + size_t(kStages) * kStageBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + kStages);
-    __shared__ int s_abort;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + size_t(kStages) * kStageBytes);   // full[2] empty[2] accum
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+    volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* s_issued = s_abort + 1;
+    volatile int* s_consumed = s_abort + 2;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int f = blockIdx.z;
-    const float2* Gc = G + f * sG;
-    float* Gf = reinterpret_cast<float*>(G + f * sG);
-    const int64_t ldf = 2 * int64_t(ld);           // floats per row
-    const int rt = r0 + blockIdx.y * kTM;          // first C row of the tile
-    const int nt = c0 + blockIdx.x * (kTN / 2);    // first complex C column of the tile
-    const int Kr = 2 * K;                          // real K
+    const int bx = blockIdx.x, by = blockIdx.y, f = blockIdx.z;
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
+                   accum = smem_u32(&bars[2 * kStages]);
 
     if (tid == 0) {
-        s_abort = 0;
-        for (int s = 0; s < kStages; ++s)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])));
+        *s_abort = 0;
+        *s_issued = 0;
+        *s_consumed = 0;
+        for (int i = 0; i < 2 * kStages + 1; ++i)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmC)) : "memory");
     }
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -172,154 +252,203 @@ __global__ void __launch_bounds__(kThreads, 1) tc_update_kernel(float2* G, int64
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tmem_slot;
 
-    // global -> registers for slice sl
-    auto load_slice = [&](int sl, SliceRegs& R) {
-        const int kb = sl * kTK;
-#pragma unroll
-        for (int it = 0; it < kAItems; ++it) {
-            const int idx = tid + it * kThreads;
-            const int r = idx >> 3, c = idx & 7;           // row, 16-byte chunk
-            const int gr = rt + r, gk = kb + 4 * c;        // real k of the chunk's first float
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (gr < r1) {
-                const float* src = Gf + int64_t(gr) * ldf + 2 * k0 + gk;
-                if (gk + 3 < Kr && (reinterpret_cast<uintptr_t>(src) & 15u) == 0) {
-                    v = *reinterpret_cast<const float4*>(src);   // only when the address is 16-byte aligned
-                } else {
-                    if (gk + 0 < Kr) v.x = src[0];
-                    if (gk + 1 < Kr) v.y = src[1];
-                    if (gk + 2 < Kr) v.z = src[2];
-                    if (gk + 3 < Kr) v.w = src[3];
-                }
+    if (tid == 0) {
+        // TMA producer
+        int kt = 0;
+        for (; kt < a.nk; ++kt) {
+            const int s = kt % kStages;
+            if (kt >= kStages && !mbar_wait(empty0 + 8u * s, uint32_t((kt / kStages - 1) & 1), a.limit)) {
+                *s_abort = 1;
+                break;
             }
-            R.a[it] = v;
+            if (*s_abort) break;
+            const uint32_t base = ops_s + uint32_t(s) * kStageBytes;
+            const uint32_t fb = full0 + 8u * s;
+            expect_tx(fb, kStageBytes);
+            const int x = kt * kTKf;
+            tma_load3(base, &tmA, x, by * kTM, 2 * f, fb);
+            tma_load3(base + kABytes, &tmA, x, by * kTM, 2 * f + 1, fb);
+            tma_load3(base + 2 * kABytes, &tmB, x, bx * kTN, 2 * f, fb);
+            tma_load3(base + 2 * kABytes + kBBytes, &tmB, x, bx * kTN, 2 * f + 1, fb);
         }
-#pragma unroll
-        for (int it = 0; it < kBItems; ++it) {
-            const int idx = tid + it * kThreads;
-            const int c = idx >> 7, nn = idx & 127;        // chunk c covers complex k 2c, 2c+1 of the slice
-            const int n = nt + nn;
-            const int j = (kb >> 1) + 2 * c;               // complex k within the panel
-            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-            if (n < c1) {
-                if (j < K) v0 = Gc[int64_t(k0 + j) * ld + n];
-                if (j + 1 < K) v1 = Gc[int64_t(k0 + j + 1) * ld + n];
+        *s_issued = kt;
+    } else if (tid == 32) {
+        // MMA issuer
+        int kt = 0;
+        for (; kt < a.nk; ++kt) {
+            const int s = kt % kStages;
+            if (!mbar_wait(full0 + 8u * s, uint32_t((kt / kStages) & 1), a.limit)) {
+                *s_abort = 1;
+                break;
             }
-            R.b0[it] = v0;
-            R.b1[it] = v1;
-        }
-    };
-    // registers -> split, swizzled shared memory of stage st
-    auto store_slice = [&](int st, const SliceRegs& R) {
-        const uint32_t base = ops_s + uint32_t(st) * kStageBytes;
-        const uint32_t Ahi = base, Alo = base + kABytes, Bhi = base + 2 * kABytes, Blo = base + 2 * kABytes + kBBytes;
-#pragma unroll
-        for (int it = 0; it < kAItems; ++it) {
-            const int idx = tid + it * kThreads;
-            const int r = idx >> 3, c = idx & 7;
-            const uint32_t o = sw128_chunk(r, c);
-            put_split(Ahi + o, Alo + o, R.a[it]);
-        }
-#pragma unroll
-        for (int it = 0; it < kBItems; ++it) {
-            const int idx = tid + it * kThreads;
-            const int c = idx >> 7, nn = idx & 127;
-            const float2 p = R.b0[it], q = R.b1[it];
-            // row 2n: (Br, -Bi) per complex k; row 2n+1: (Bi, Br)
-            const uint32_t o0 = sw128_chunk(2 * nn, c), o1 = sw128_chunk(2 * nn + 1, c);
-            put_split(Bhi + o0, Blo + o0, make_float4(p.x, -p.y, q.x, -q.y));
-            put_split(Bhi + o1, Blo + o1, make_float4(p.y, p.x, q.y, q.x));
-        }
-    };
-
-    const int nslices = (Kr + kTK - 1) / kTK;
-    uint32_t phase[kStages] = {0, 0};
-    SliceRegs regs;
-    load_slice(0, regs);
-    for (int sl = 0; sl < nslices; ++sl) {
-        const int st = sl % kStages;
-        if (sl >= kStages) {   // the MMAs that read this buffer must be done
-            if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) {
-                if (tid == 0) { s_abort = 1; atomicExch(err, 1); }
+            if (*s_abort) {
+                ++kt;   // this stage's loads have landed: nothing left in flight for it
+                break;
             }
-            phase[st] ^= 1u;
-        }
-        __syncthreads();
-        if (s_abort) break;
-        store_slice(st, regs);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t base = ops_s + uint32_t(st) * kStageBytes;
-            const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes, blo = base + 2 * kABytes + kBBytes;
+            const uint32_t base = ops_s + uint32_t(s) * kStageBytes;
+            const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes,
+                           blo = base + 2 * kABytes + kBBytes;
 #pragma unroll
-            for (int s = 0; s < kTK / 8; ++s) {   // K = 8 per MMA: 32 bytes along the swizzle row
-                const uint32_t off = uint32_t(s) * 32u;
-                const uint32_t first = (sl == 0 && s == 0) ? 0u : 1u;
+            for (int ks = 0; ks < kTKf / 8; ++ks) {   // K = 8 per MMA: 32 bytes along the swizzle row
+                const uint32_t off = uint32_t(ks) * 32u;
+                const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
                 mma_tf32(tmem, make_desc(ahi + off), make_desc(bhi + off), first);
                 mma_tf32(tmem + 256u, make_desc(ahi + off), make_desc(blo + off), first);
                 mma_tf32(tmem + 256u, make_desc(alo + off), make_desc(bhi + off), 1u);
             }
-            mma_commit(smem_u32(&mbar[st]));
+            mma_commit(empty0 + 8u * s);
         }
-        if (sl + 1 < nslices) load_slice(sl + 1, regs);   // overlaps the MMAs just issued
-    }
-    // the last commit tracks every MMA issued before it
-    if (!s_abort) {
-        const int st = (nslices - 1) % kStages;
-        if (!mbar_wait(smem_u32(&mbar[st]), phase[st])) {
-            if (tid == 0) atomicExch(err, 1);
-            s_abort = 1;
-        }
-    }
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (!s_abort) {
-        // warp w: TMEM lanes 32*(w%4).., column half w/4; staged through its own 32 x 33 tile
-        float* tile = reinterpret_cast<float*>(ops) + warp * (32 * 33);
-        const int lane_base = (warp & 3) * 32;
-        const int half = warp >> 2;
-        for (int cb = half * 128; cb < half * 128 + 128; cb += 32) {
-            uint32_t v[32], u[32];
-            const uint32_t taddr = tmem + (uint32_t(lane_base) << 16) + uint32_t(cb);
-            tmem_ld32(taddr, v);
-            tmem_ld32(taddr + 256u, u);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        *s_consumed = kt;
+        mma_commit(accum);   // tracks every MMA issued above
+    } else if (warp >= 4) {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
+        const bool ok = mbar_wait(accum, 0u, a.limit);
+        if (!ok) *s_abort = 1;
+        if (ok && !*s_abort) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int q = warp & 3;
+            const uint32_t stage0 = ops_s + uint32_t(warp - 4) * 8192u;   // operand ring is idle now
+            const uint32_t trow = tmem + (uint32_t(32 * q) << 16);
+            const int y = a.cy0 + by * kTM + 32 * q;
+            const int nch = y < a.cy1 ? min(kTN / 32, (a.cx1 - a.cx0 - bx * kTN + 31) / 32) : 0;
+            for (int ch = 0; ch < nch; ++ch) {
+                uint32_t v[32], u[32];
+                tmem_ld32(trow + uint32_t(ch * 32), v);
+                tmem_ld32(trow + 256u + uint32_t(ch * 32), u);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                const uint32_t stg = stage0 + uint32_t(ch & 1) * 4096u;
+                if (ch >= 2) {
+                    if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+                    __syncwarp();
+                }
 #pragma unroll
-            for (int j = 0; j < 32; ++j) tile[lane * 33 + j] = __uint_as_float(v[j]) + __uint_as_float(u[j]);
-            __syncwarp();
-            const int q = 2 * nt + cb + lane;             // real column of C handled by this lane
-            const bool qok = q < 2 * c1;
-            for (int rr = 0; rr < 32; ++rr) {
-                const int row = rt + lane_base + rr;
-                if (row < r1 && qok) Gf[int64_t(row) * ldf + q] -= tile[rr * 33 + lane];
+                for (int c4 = 0; c4 < 8; ++c4) {
+                    const float x0 = -(__uint_as_float(v[4 * c4 + 0]) + __uint_as_float(u[4 * c4 + 0]));
+                    const float x1 = -(__uint_as_float(v[4 * c4 + 1]) + __uint_as_float(u[4 * c4 + 1]));
+                    const float x2 = -(__uint_as_float(v[4 * c4 + 2]) + __uint_as_float(u[4 * c4 + 2]));
+                    const float x3 = -(__uint_as_float(v[4 * c4 + 3]) + __uint_as_float(u[4 * c4 + 3]));
+                    const uint32_t addr = stg + uint32_t(lane) * 128u + (uint32_t(c4 ^ (lane & 7)) << 4);
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x0), "f"(x1), "f"(x2),
+                                 "f"(x3)
+                                 : "memory");
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    tma_reduce_add3(&tmC, a.cx0 + bx * kTN + ch * 32, y, f, stg);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                }
+                __syncwarp();
             }
+            if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
             __syncwarp();
         }
     }
+    __syncthreads();
+    // drain: loads and MMAs already issued finish before shared or tensor memory is released
+    if (tid == 0) {
+        bool ok = true;
+        for (int kt = *s_consumed; kt < *s_issued; ++kt)
+            ok = mbar_wait(full0 + 8u * (kt % kStages), uint32_t((kt / kStages) & 1), kDrainSpin) && ok;
+        if (!ok || *s_abort) atomicExch(a.err, 1);
+    }
+    if (tid == 32 && !mbar_wait(accum, 0u, kDrainSpin)) atomicExch(a.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
     }
 }
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
+inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// 3-D FP32 tensor map: inner dimension d0 (contiguous), rows d1 (stride s1 bytes), planes d2 (stride s2).
+bool encode3(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
+             uint32_t box0, uint32_t box1, CUtensorMapL2promotion l2) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {d0, d1, d2};
+    const cuuint64_t strides[2] = {s1, s2};
+    const cuuint32_t box[3] = {box0, box1, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, l2, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int64_t pack_floats(int64_t rows, int64_t Kp) { return 2 * rows * Kp; }
 
 }  // namespace
 
-void launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
-                      int32_t* err, cudaStream_t st) {
-    if (r1 <= r0 || c1 <= c0 || K <= 0) return;
+void set_tc_spin_limit(uint32_t spins) { g_spin_limit.store(spins ? spins : kDefaultSpin); }
+
+size_t tc_workspace_bytes(int F, int m, int ncols, int npiv) {
+    const int64_t nb = std::min(128, npiv);
+    const int64_t Kpn = round_up(2 * int64_t(npiv), kTKf), Kp1 = round_up(2 * nb, kTKf);
+    int64_t a = pack_floats(m - nb, Kp1);
+    a = std::max(a, pack_floats(std::min(128, npiv), Kpn));
+    a = std::max(a, pack_floats(m - npiv, Kpn));
+    int64_t b = pack_floats(2 * (npiv - nb), Kp1);
+    b = std::max(b, pack_floats(2 * int64_t(ncols - npiv), Kpn));
+    return size_t(F) * size_t(a + b) * sizeof(float) + 1024;
+}
+
+bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
+                      const TcCtx& tc, cudaStream_t st) {
+    if (r1 <= r0 || c1 <= c0 || K <= 0) return true;
+    // TMA: 16-byte aligned base and row / matrix strides, tile columns start on 16-byte boundaries
+    if ((reinterpret_cast<uintptr_t>(G) & 15) || (ld & 1) || (sG & 1) || (c0 & 1)) return false;
+    const int M = r1 - r0, N = c1 - c0;
+    const int64_t Kp = round_up(2 * int64_t(K), kTKf);
+    const int64_t aF = int64_t(F) * pack_floats(M, Kp), bF = int64_t(F) * pack_floats(2 * int64_t(N), Kp);
+    const size_t need = size_t(aF + bF) * sizeof(float) + 256;
+    if (!tc.ws || need > tc.ws_bytes) return false;
+    float* Ap = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tc.ws) + 255) & ~uintptr_t(255));
+    float* Bp = Ap + aF;   // aF is a multiple of 64 floats: Bp stays 256-byte aligned
+
+    CUtensorMap mA, mB, mC;
+    if (!encode3(&mA, Ap, Kp, M, 2 * uint64_t(F), Kp * 4, uint64_t(M) * Kp * 4, kTKf, kTM,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mB, Bp, Kp, 2 * uint64_t(N), 2 * uint64_t(F), Kp * 4, 2 * uint64_t(N) * Kp * 4, kTKf, kTN,
+                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mC, G, 2 * uint64_t(c1), uint64_t(r1), uint64_t(F), uint64_t(ld) * 8, uint64_t(sG) * 8, 32, 32,
+                 CU_TENSOR_MAP_L2_PROMOTION_NONE))
+        return false;
+
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(tc_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
+        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
         attr_set = true;
     }
-    dim3 grid(cdiv(int64_t(c1 - c0), kTN / 2), cdiv(r1 - r0, kTM), F);
-    ProfScope ps(PK_GEMM, 8.0 * F * double(r1 - r0) * double(c1 - c0) * K, st);
-    tc_update_kernel<<<grid, kThreads, kSmemBytes, st>>>(G, sG, ld, r0, r1, c0, c1, k0, K, err);
+    {
+        ProfScope ps(PK_PACK, 0.0, st);
+        pack_a_kernel<<<dim3(cdiv(int64_t(M) * Kp / 4, 256), F), 256, 0, st>>>(
+            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 2 * k0, 2 * K, int(Kp), Ap);
+        pack_b_kernel<<<dim3(cdiv(Kp / 2, 32), cdiv(N, 32), F), dim3(32, 8), 0, st>>>(G, sG, ld, k0, K, c0, N, int(Kp),
+                                                                                        Bp);
+    }
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTKf), g_spin_limit.load(), tc.err};
+    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
+    ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
+    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, st>>>(mA, mB, mC, args);
+    return true;
 }
 
 }  // namespace fsi

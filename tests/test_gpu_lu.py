@@ -56,3 +56,61 @@ def test_singular_matrix_is_reported():
     At = torch.tensor(A, device="cuda")
     ipiv, nsing = api.fsi_batched_lu(At, 40)
     assert nsing == 1
+
+
+def _lu_residual(A, R, piv, npiv):
+    PA = _apply_ipiv(A, piv)
+    L = np.tril(R[:, :npiv], -1)
+    L[np.arange(npiv), np.arange(npiv)] = 1.0
+    U = np.triu(R[:npiv, :])
+    S = np.zeros_like(PA)
+    S[npiv:, npiv:] = R[npiv:, npiv:]
+    return np.linalg.norm(L @ U + S - PA) / np.linalg.norm(A)
+
+
+def test_tensor_core_updates_on_a_slab_window():
+    """A config-2 slab window (2b x 3b, b = 852, b pivots): every trailing update of the lazy
+    order (K = 128 panel updates, the left-looking solve of U12 with K up to 724, the Schur
+    update with K = 852) on the tcgen05 path; |PA - LU| at FP32 level, like the SIMT factor."""
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    b = 852
+    rng = np.random.default_rng(852)
+    A = rng.standard_normal((2, 2 * b, 3 * b)) + 1j * rng.standard_normal((2, 2 * b, 3 * b))
+    errs = {}
+    for tc in (False, True):
+        At = torch.tensor(A.astype(np.complex64), device="cuda")
+        ipiv, nsing = api.fsi_batched_lu(At, b, tensor_cores=tc)
+        torch.cuda.synchronize()
+        assert nsing == 0
+        R = At.cpu().numpy().astype(np.complex128)
+        piv = ipiv.cpu().numpy()
+        errs[tc] = max(_lu_residual(A[i], R[i], piv[i], b) for i in range(2))
+    print("slab window |PA-LU|/|A|: simt %.2e  tcgen05 %.2e" % (errs[False], errs[True]))
+    assert errs[False] <= 2e-5 * np.sqrt(2 * b)
+    assert errs[True] <= 2.0 * errs[False] + 1e-6
+
+
+def test_tensor_core_wait_timeout_is_reported_and_the_next_call_is_clean():
+    """With a spin limit of one poll the bounded mbarrier waits of the tensor-core update give
+    up: the call returns FSI_ETIMEOUT after the kernel has waited for the loads and MMAs it had
+    issued and freed its tensor memory; with the default limit the next call factors correctly."""
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    rng = np.random.default_rng(5)
+    m, ncols, npiv = 600, 900, 300
+    A = rng.standard_normal((2, m, ncols)) + 1j * rng.standard_normal((2, m, ncols))
+    At = torch.tensor(A.astype(np.complex64), device="cuda")
+    api.fsi_set_wait_limit(1)
+    try:
+        with pytest.raises(RuntimeError, match="timed out"):
+            api.fsi_batched_lu(At, npiv, tensor_cores=True)
+    finally:
+        api.fsi_set_wait_limit(0)
+    At = torch.tensor(A.astype(np.complex64), device="cuda")
+    ipiv, nsing = api.fsi_batched_lu(At, npiv, tensor_cores=True)
+    torch.cuda.synchronize()
+    assert nsing == 0
+    R = At.cpu().numpy().astype(np.complex128)
+    piv = ipiv.cpu().numpy()
+    assert max(_lu_residual(A[i], R[i], piv[i], npiv) for i in range(2)) <= 2e-5 * np.sqrt(m)

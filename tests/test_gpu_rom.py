@@ -177,3 +177,74 @@ def test_windows_match_oracle_windows(reuse):
         ref.append(rom.reduced_sweep(x["rm"], [f])[0])
     # poorly converged windows amplify basis rounding in their outputs (as in the greedy test)
     assert rel(p.cpu().numpy(), np.array(ref)) <= 1e-4
+
+
+def _small_rom(floor=True):
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    w = W.small_model(floor=floor)
+    spec = w.model
+    model = api.fsi_assemble(spec)
+    F = api.dense_loads(spec, w.loads, w.n_rhs)
+    rcv = torch.tensor(api.receiver_dofs(spec, w.receivers), device="cuda")
+    shifts = [60.0, 150.0, 250.0]
+    V = api.rom_build(model, shifts, 3, F, kmax=200, precision="fp32_ir", tol=1e-12, max_refine=30)
+    return api, w, model, F, rcv, shifts, V, api.rom_project(model, V, F, rcv)
+
+
+def test_rom_save_load_round_trip_on_the_device(tmp_path):
+    """A reduced model (matrices, expansion points, basis) written from device buffers and read
+    back gives bit-identical buffers and the same reduced sweep."""
+    torch = need_cuda()
+    api, w, model, F, rcv, shifts, V, rm = _small_rom()
+    path = str(tmp_path / "small.fsirom")
+    api.rom_save(path, rm, shifts, V=V, band=(20.0, 300.0))
+    r2, sh2, V2, band = api.rom_load(path)
+    for a, b in ((rm.KR, r2.KR), (rm.DR, r2.DR), (rm.MR, r2.MR), (rm.fR, r2.fR), (rm.CR, r2.CR), (V, V2)):
+        assert torch.equal(a.contiguous(), b.contiguous())
+    assert list(sh2) == shifts and band == (20.0, 300.0)
+    freqs = np.array([45.0, 133.0, 280.0])
+    p1, _ = api.rom_sweep(rm, freqs, batch=3)
+    p2, _ = api.rom_sweep(r2, freqs, batch=3)
+    assert torch.equal(p1, p2)
+
+
+def test_rom_sweep_fp32_refined_matches_fp64():
+    """rom_sweep with precision FSI_FP32_IR (FP32 LU refined against the FP64 residual, FP64
+    re-solve where the refinement stalls) against the FP64 reduced LU and the oracle's ROM."""
+    torch = need_cuda()
+    api, w, model, F, rcv, shifts, V, rm = _small_rom()
+    freqs = np.linspace(30.0, 290.0, 27)
+    p64, spl64 = api.rom_sweep(rm, freqs, batch=8)
+    p32, spl32, fb = api.rom_sweep(rm, freqs, batch=8, precision="fp32_ir", return_fp64=True)
+    a, b = p32.cpu().numpy(), p64.cpu().numpy()
+    errs = np.array([rel(a[i], b[i]) for i in range(len(freqs))])
+    print("fp32_ir vs fp64 reduced sweep: max %.2e, FP64 re-solves %d" % (errs.max(), int(fb.sum())))
+    assert errs.max() <= 1e-6
+    assert np.abs(spl32.cpu().numpy() - spl64.cpu().numpy()).max() <= 1e-5
+
+
+def test_check_and_resolve_replaces_failing_frequencies_by_full_order():
+    """rom_check_resolve judges every frequency by the full-order FP64 residual of the lifted
+    reduced solution.  With res_tol = 0 every frequency fails the check (a planted failure) and
+    its outputs must become the full-order ones; with a loose tolerance nothing changes."""
+    torch = need_cuda()
+    api, w, model, F, rcv, shifts, V, rm = _small_rom()
+    freqs = np.array([45.0, 97.0, 150.0, 212.0, 280.0])
+    p, spl = api.rom_sweep(rm, freqs, batch=5)
+    keep_p, keep_spl = p.clone(), spl.clone()
+    rel_l, res_l, n_l = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=1.0)
+    assert n_l == 0 and not res_l.any() and torch.equal(p, keep_p) and torch.equal(spl, keep_spl)
+    ref = api.rom_residual_check(model, V, rm, F, freqs)
+    assert np.allclose(rel_l, ref, rtol=1e-12, atol=0)
+    rel_0, res_0, n_0 = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=0.0)
+    assert n_0 == len(freqs) and res_0.all()
+    full = api.frf_sweep_full(model, freqs, F, rcv, precision="fp32_ir", batch=5, max_refine=60, tol=1e-10)
+    # the same kernels and batch as the call's re-solve (sums of atomically reduced norms may
+    # round differently from run to run)
+    assert rel(p.cpu().numpy(), full.p.cpu().numpy()) <= 1e-11
+    assert np.abs(spl.cpu().numpy() - full.spl.cpu().numpy()).max() <= 1e-9
+    asm = fem.assemble(w.model)
+    y, _ = fom.sweep(asm, freqs, fem.load_matrix(w.model, w.loads, w.n_rhs), fem.receiver_dofs(w.model, w.receivers),
+                     method="dense")
+    assert rel(p.cpu().numpy(), y) <= 1e-8
