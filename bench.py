@@ -4,11 +4,12 @@ Workload (the model the headline metric is quoted on): 1.5 x 1.5 x 6 m cavity
 at 24 x 24 x 96 nodes plus the shell ring, 81,792 DoF (b = 852 per slab, 96
 slabs), floor impedance, 4 seeded shell loads, 32 receivers, 481 frequencies
 20..500 Hz.  A step is one batch of `--batch` frequencies through the whole
-path: form A(w) -> block-banded LU in FP32 -> FP64 GMRES refinement
-preconditioned by the FP32 factor, to a relative residual of 1e-10 ->
-receivers and SPL.  value = frequencies / s over
-all ranks.  The factor store of one batch (~70 GB) is far larger than L2, so no
-separate L2 flush is needed between steps.
+path: form A(w) -> block-banded LU stored in FP32 (the long trailing updates on
+the tcgen05 tensor cores with three-plane BF16 splits, --precision bf16x6_ir;
+or all on the FP32 pipe, fp32_ir) -> FP64 GMRES refinement preconditioned by the
+factor, to a relative residual of 1e-10 -> receivers and SPL.  value =
+frequencies / s over all ranks.  The factor store of one batch (~200 GB) is far
+larger than L2, so no separate L2 flush is needed between steps.
 
 --impl reference times the CPU oracle (oracle/, the plain FP64 restatement of
 the method) on the host cores on a bounded sample of the same workload.
@@ -153,6 +154,37 @@ def cpu_baseline_sample(seconds_cap=40.0):
                       f"in FP64, {dt:.1f} s"}
 
 
+def _sm_count(torch):
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
+def measure_peaks(api, kinds=("fp32_fma", "fp64_fma", "bf16_tcgen05", "tf32_tcgen05"), seconds=0.25):
+    """Throughput probes of the execution units (fsi_probe_peak), TFLOP/s."""
+    out = {}
+    for k in kinds:
+        try:
+            out[k] = api.fsi_probe_peak(k, seconds)[0]
+        except RuntimeError as e:   # a probe that fails leaves the derived figure in use
+            out[k] = None
+            print(f"peak probe {k} failed: {e}", file=sys.stderr)
+    return out
+
+
+def run_peaks(args):
+    """Measured FP32 / FP64 FMA and tcgen05 BF16 / TF32 throughput of this GPU (one line)."""
+    import torch
+    from paper_2310_04734_gb300 import api
+    clocks = ClockSampler(0)
+    clocks.start()
+    probes = measure_peaks(api, seconds=1.0)
+    clk = clocks.stop()
+    peaks, src = _peaks()
+    print(json.dumps({"mode": "peaks", "tflops": probes, "sm_count": _sm_count(torch), "clocks": clk,
+                      "measured_peaks_json": {k: peaks.get(k) for k in ("hbm_gbs", "bf16_tflops",
+                                                                        "bf16_tflops_sustained")}}))
+    return 0
+
+
 def run_lu_window(args):
     """Batched partial LU of --batch random windows shaped like one config-2 slab step
     (2b x 3b complex, b = 852, b pivots): the factor kernels alone, a few hundred MB."""
@@ -163,7 +195,7 @@ def run_lu_window(args):
     gen = torch.Generator(device="cuda").manual_seed(7)
     base = torch.randn((args.batch, m, ncols), dtype=torch.complex64, device="cuda", generator=gen)
     A = base.clone()
-    tc = args.precision == "tf32x3_ir"
+    tc = {"bf16x6_ir": "bf16x6", "bf16_ir": "bf16"}.get(args.precision, False)
     for _ in range(args.warmup):
         A.copy_(base)
         api.fsi_batched_lu(A, b, tensor_cores=tc)
@@ -254,9 +286,9 @@ def run_design(args):
     frequencies each): the error estimator is trained on the first 16 variants' greedy
     ROMs by the GPU training kernel; variants 0-15 get residual-driven greedy ROMs and
     16-63 estimator-driven ones; all 64 reduced sweeps run in one persistent launch
-    replayed from a CUDA graph (timed); every variant is checked against the full-order
-    model at 40 seeded frequencies, and frequencies above 0.1 dB count as re-solved at
-    full order."""
+    replayed from a CUDA graph (timed); every variant is checked at 40 seeded frequencies
+    by the full-order residual of its lifted reduced solutions, and frequencies above
+    the residual tolerance are re-solved at full order and replaced (rom_check_resolve)."""
     import torch
     from paper_2310_04734_gb300 import api, design_study as ds
     variants = W.config5_reduced_variants(64)
@@ -302,16 +334,32 @@ def run_design(args):
     nfreq = sum(len(w.freqs_hz) for w in variants)
     # reduced systems the FP32 factor could not refine are re-solved in FP64 (not timed)
     nfix = ms.fixup(roms, [w.freqs_hz for w in variants])
-    # checks at 40 seeded frequencies per variant
-    worst, resolve, kk, resid = [], 0, [], []
+    # checks at 40 seeded frequencies per variant: the full-order FP64 residual of the lifted
+    # reduced solutions judges each one (rom_check_resolve); failures are re-solved at full
+    # order and replace the reduced outputs.  The SPL error of the final outputs against the
+    # full-order sweep is then measured at the same frequencies (a report, not part of the path).
+    worst, worst_before, resolve, kk, resid = [], [], 0, [], []
+    torch.cuda.synchronize()
+    t_check = 0.0
     for i, w in enumerate(variants):
         idx = np.sort(np.random.default_rng([w.config_id, 3]).choice(len(w.freqs_hz), size=40, replace=False))
-        # FP64 full-order residual of the lifted reduced solutions (CSR residual kernel)
-        model_i, F_i, _ = handles[i]
-        resid.append(float(api.rom_residual_check(model_i, bases[i], roms[i], F_i, w.freqs_hz[idx]).max()))
-        db, _ = ds.check_variant(w, handles[i], ms.p[i], idx)
+        model_i, F_i, rcv_i = handles[i]
+        ti = torch.as_tensor(idx, device="cuda")
+        pc, sc = ms.p[i][ti].contiguous(), ms.spl[i][ti].contiguous()
+        before = pc.clone()
+        t0 = time.perf_counter()
+        rel, res, n = api.rom_check_resolve(model_i, bases[i], roms[i], F_i, rcv_i, w.freqs_hz[idx], pc, sc,
+                                            res_tol=args.design_res_tol)
+        torch.cuda.synchronize()
+        t_check += time.perf_counter() - t0
+        ms.p[i][ti] = pc
+        ms.spl[i][ti] = sc
+        resolve += n
+        resid.append(float(rel.max()))
+        db, pf = ds.check_variant(w, handles[i], ms.p[i], idx)
+        db0 = np.abs(20.0 * np.log10(np.abs(before.cpu().numpy()) / np.abs(pf))).max(axis=(1, 2))
         worst.append(float(db.max()))
-        resolve += int((db > 0.1).sum())
+        worst_before.append(float(db0.max()))
         kk.append(int(roms[i].k))
     worst = np.array(worst)
     print(json.dumps({
@@ -319,13 +367,17 @@ def run_design(args):
         "value": nfreq / t_sweep, "unit": UNIT, "variants": len(variants), "frequencies": nfreq,
         "sweep_ms": t_sweep * 1e3, "train_s": t_train, "build_s": t_build, "fp64_resolved_reduced": nfix,
         "estimator_final_loss": float(np.mean(losses[-100:])), "k": {"min": min(kk), "max": max(kk)},
-        "check": {"frequencies": 40 * len(variants), "resolved_full_order": resolve,
+        "check": {"frequencies": 40 * len(variants), "residual_tol": args.design_res_tol,
+                  "resolved_full_order": resolve, "check_and_resolve_s": t_check,
+                  "max_spl_err_db_before_check": float(max(worst_before)),
+                  "max_spl_err_db_after_check": float(worst.max()),
                   "max_full_residual": float(max(resid)), "median_variant_max_full_residual": float(np.median(resid)),
                   "max_spl_err_db_residual_driven": float(worst[:16].max()),
                   "max_spl_err_db_estimator_driven": float(worst[16:].max()),
                   "median_worst_db_residual_driven": float(np.median(worst[:16])),
                   "median_worst_db_estimator_driven": float(np.median(worst[16:]))},
-        "e2e": {"value": nfreq / (t_build + t_sweep), "unit": UNIT, "note": "ROM builds + one sweep"},
+        "e2e": {"value": nfreq / (t_build + t_sweep + t_check), "unit": UNIT,
+                "note": "ROM builds + one sweep + the residual check and full-order re-solves"},
         "dtype": "f32 reduced LU + f64 refinement; estimator fp16 weights / fp32 accumulation"}))
     return 0
 
@@ -394,10 +446,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=96)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--precision", default="fp32_ir", choices=["fp32_ir", "tf32x3_ir", "fp64"])
+    ap.add_argument("--precision", default="bf16x6_ir", choices=["fp32_ir", "bf16x6_ir", "bf16_ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--fp64-sample", type=int, default=2, help="frequencies timed on the plain FP64 path")
+    ap.add_argument("--fp64-sample", type=int, default=4, help="frequencies timed on the plain FP64 path")
     ap.add_argument("--rom-band", type=float, nargs=2, default=[1.0, 1000.0])
     ap.add_argument("--rom-q", type=int, default=16)
     ap.add_argument("--rom-kmax", type=int, default=400)
@@ -406,7 +458,9 @@ def main():
     ap.add_argument("--rom-no-reuse", action="store_true",
                     help="windows start from fresh points instead of their enclosing windows' points")
     ap.add_argument("--design-shifts", type=int, default=16)
-    ap.add_argument("--mode", default="sweep", choices=["sweep", "lu_window", "rom", "design", "kernels"],
+    ap.add_argument("--design-res-tol", type=float, default=1e-6,
+                    help="full-order relative residual above which a check frequency is re-solved at full order")
+    ap.add_argument("--mode", default="sweep", choices=["sweep", "lu_window", "rom", "design", "kernels", "peaks"],
                     help="lu_window: only the batched band-LU of config-2-sized windows (for kernel profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -419,6 +473,8 @@ def main():
         return run_design(args)
     if args.mode == "kernels":
         return run_kernels(args)
+    if args.mode == "peaks":
+        return run_peaks(args)
 
     import torch
     from paper_2310_04734_gb300 import api
@@ -470,17 +526,21 @@ def main():
     torch.cuda.nvtx.range_push("timed")
     ev0.record(stream)
     for s in range(args.warmup, nsteps):
-        r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, profile=True, **kw)
+        r = api.frf_sweep_full(model, batch_freqs(s), F, rcv, **kw)
         unconv += int(r.stats.n_unconverged)
-        kern_ms += np.array(r.stats.kernel_ms[:])
-        kern_flops += np.array(r.stats.kernel_flops[:])
-        kern_n += np.array(r.stats.kernel_launches[:])
         launches += int(r.stats.launches)
         iters.extend(r.iters.tolist())
     ev1.record(stream)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     clk = clocks.stop()
+    # per-kernel times from a separate pass over the first timed batch (events around every
+    # launch), so the headline comes from the un-instrumented steps
+    rp = api.frf_sweep_full(model, batch_freqs(args.warmup), F, rcv, profile=True, **kw)
+    kern_ms += np.array(rp.stats.kernel_ms[:])
+    kern_flops += np.array(rp.stats.kernel_flops[:])
+    kern_n += np.array(rp.stats.kernel_launches[:])
+    prof_ms = float(sum(rp.stats.kernel_ms[:]))
     t_ms = ev0.elapsed_time(ev1)
     if pg:
         t = torch.tensor([t_ms], device="cuda", dtype=torch.float64)
@@ -498,7 +558,7 @@ def main():
         rh = rcv.cpu().numpy()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ne = max(1, min(2, args.steps))
+        ne = max(1, min(3, args.steps))
         for s in range(ne):   # the timed steps' frequencies again
             api.frf_sweep_full(model, batch_freqs(args.warmup + s), Fview, rh, host_io=True, **kw)
         torch.cuda.synchronize()
@@ -511,7 +571,8 @@ def main():
     # plain FP64 full-order sweep on the same GPU (the metric's denominator), sampled
     fp64 = None
     if args.fp64_sample > 0:
-        fs = batch_freqs(0)[:args.fp64_sample]
+        # seeded frequencies spread over the band (config 2's check-frequency stream)
+        fs = np.sort(np.random.default_rng([2, 3]).choice(freqs, size=args.fp64_sample, replace=False))
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         r64 = api.frf_sweep_full(model, fs, F, rcv, precision="fp64", batch=len(fs), max_refine=1)
@@ -526,32 +587,55 @@ def main():
                 "max_rel_err_mixed_vs_fp64": float(np.max(np.abs(pm - p64) / np.abs(p64)))}
 
     peaks, src = _peaks()
-    # dominant kernel: the FP32 complex GEMM update (SIMT FMA pipe); its peak is derived from
-    # 152 SMs x 128 FP32 lanes x 2 flop x the maximum SM clock
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    g = 10 if args.precision == "tf32x3_ir" else 0
-    achieved = kern_flops[g] / (kern_ms[g] / 1e3) / 1e12 if kern_ms[g] > 0 else None
-    if args.precision == "tf32x3_ir":
-        # tensor pipe: TF32 dense peak = half the measured BF16 burst peak (nominal ratio 1:2);
-        # 3 TF32 products per algorithmic flop
-        tf32_peak = float(peaks["bf16_tflops"]) / 2.0
-        roofline = {"bound": "tensor", "kernel": "tc_update_kernel (tcgen05 kind::tf32, 3xTF32 trailing update)",
-                    "achieved": achieved, "peak": tf32_peak / 3.0, "unit": "TFLOP/s",
-                    "frac": (achieved / (tf32_peak / 3.0)) if achieved else None, "traffic": None,
-                    "peak_source": f"measured bf16 {peaks['bf16_tflops']} TFLOP/s x 1/2 (tf32) x 1/3 (3 products)",
-                    "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
+    b, nz = int(model.dims.b), int(model.dims.nz)
+    # SURVEY 8(d) counts (8/3 + 8) b^3 real flops per slab step of the block LU (the coupling
+    # blocks are sparse); the band LU with pivoting across the stacked panel of two slabs executes
+    # sum_j 8 (2b - j)(3b - j) = 8 (6 - 5/2 + 1/3) b^3 = 30.67 b^3, so each launch's executed
+    # count is credited with the fraction alg_frac of algorithmic work
+    alg_step = (8.0 / 3.0 + 8.0) * b ** 3
+    exec_step = 8.0 * (6.0 - 2.5 + 1.0 / 3.0) * b ** 3
+    alg_frac = alg_step / exec_step
+    alg_per_freq = alg_step * (nz - 1)
+    tensor = args.precision in ("bf16x6_ir", "bf16_ir")
+    g = 10 if tensor else 0
+    t_dom = kern_ms[g] / 1e3
+    exec_rate = kern_flops[g] / t_dom / 1e12 if t_dom > 0 else None
+    alg_rate = exec_rate * alg_frac if exec_rate else None
+    probes = measure_peaks(api, ("fp32_fma", "bf16_tcgen05") if not tensor else ("bf16_tcgen05", "fp32_fma"))
+    if tensor:
+        nprod = 6 if args.precision == "bf16x6_ir" else 1
+        peak = float(peaks["bf16_tflops"]) / nprod
+        roofline = {"bound": "tensor",
+                    "kernel": f"tc_gemm_kernel (tcgen05 kind::f16, BF16 operands, {nprod} product(s) per term, TMA-fed)",
+                    "achieved": alg_rate, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (alg_rate / peak) if alg_rate else None,
+                    "achieved_executed": exec_rate, "frac_executed": (exec_rate / peak) if exec_rate else None,
+                    "tensor_pipe_frac": (exec_rate * nprod / float(peaks["bf16_tflops"])) if exec_rate else None,
+                    "traffic": None,
+                    "peak_source": f"of measured: bf16 {peaks['bf16_tflops']} TFLOP/s (MEASURED_PEAKS.json) / "
+                                   f"{nprod} product(s); probe of this run {probes.get('bf16_tcgen05')}"}
     else:
-        # DRAM bytes per algorithmic flop of the trailing update, from an ncu capture of the
-        # 1576 x 2428 x 128 update of eight config-2 windows (465.3 MB for 31.35 GFLOP); the
-        # C read-modify-write dominates and scales with the flops at fixed K
+        # DRAM bytes per executed flop of the trailing update, from an ncu capture (C read-modify-write)
         traffic = GEMM_BYTES_PER_FLOP * kern_flops[g] / max(kern_n[g], 1)
-        roofline = {"bound": "alu", "kernel": "cgemm_f32_kernel (trailing complex GEMM of the band LU, FP32 SIMT)",
-                    "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        derived = _sm_count(torch) * 128 * 2 * sm_max * 1e6 / 1e12
+        peak = probes.get("fp32_fma") or derived
+        roofline = {"bound": "alu", "kernel": "cgemm_f32_kernel (complex GEMM updates of the band LU, FP32 SIMT)",
+                    "achieved": alg_rate, "peak": peak, "unit": "TFLOP/s",
+                    "frac": (alg_rate / peak) if alg_rate else None,
+                    "achieved_executed": exec_rate, "frac_executed": (exec_rate / peak) if exec_rate else None,
+                    "traffic": traffic,
                     "traffic_unit": "bytes per launch (mean launch; scaled from an ncu capture)",
-                    "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
-                    "kernel_share_of_timed": float(kern_ms[g] / t_ms) if t_ms > 0 else None}
+                    "peak_source": "of measured: FP32 FMA probe of this run (fsi_probe_peak)" if probes.get("fp32_fma")
+                                   else f"derived: {_sm_count(torch)} SM x 128 FP32 lanes x 2 x {sm_max:.0f} MHz",
+                    "peak_derived": derived}
+    roofline.update({
+        "kernel_share_of_profiled": float(kern_ms[g] / max(prof_ms, 1e-9)),
+        "alg_flops_note": "achieved = executed flops x %.4f: SURVEY 8(d) counts 10.67 b^3 per slab step, the band LU "
+                          "executes 30.67 b^3 (pivoting across the stacked panel makes the coupling blocks dense)"
+                          % alg_frac,
+        "lu_alg_tflops_end_to_end": alg_per_freq * value / 1e12,
+        "measured_probes_tflops": probes})
     shares = {k: {"ms": float(kern_ms[i]), "launches": int(kern_n[i]),
                   "share": float(kern_ms[i] / max(kern_ms.sum(), 1e-9))}
               for i, k in enumerate(["gemm", "panel", "trsm", "laswp", "form", "shift", "solve_tri", "resid",
@@ -565,7 +649,8 @@ def main():
                 "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": {"fp32_ir": "f32 factor + f64 refinement",
-                          "tf32x3_ir": "f32 factor (tensor-core 3xTF32 updates) + f64 refinement",
+                          "bf16x6_ir": "f32 factor (tensor-core BF16x6 updates) + f64 refinement",
+                          "bf16_ir": "bf16 tensor-core updates, f32 factor storage + f64 refinement",
                           "fp64": "f64"}[args.precision],
                 "data": "synthetic",
                 "config": {"workload": w.name, "model_dofs": int(model.dims.n), "slab_block": int(model.dims.b),
@@ -575,7 +660,8 @@ def main():
                 "roofline": roofline, "kernels": shares, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "fp64_full_order": fp64,
                 "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters)), "unconverged": unconv,
-                                 "method": "GMRES(20) on the FP64 system, FP32 band-LU preconditioner"},
+                                 "method": "GMRES(20) on the FP64 system, preconditioned by the band LU (%s)"
+                                           % args.precision},
                 "peaks_source": src}
         print(json.dumps(line), flush=True)
     if pg:

@@ -53,8 +53,12 @@ typedef enum {
 typedef enum {
     FSI_FP64 = 0,         /* factor and solve in FP64 (the plain full-order sweep)  */
     FSI_FP32_IR = 1,      /* factor in FP32, FP64 residual iterative refinement     */
-    FSI_TF32X3_IR = 2     /* as FSI_FP32_IR, trailing updates on the tensor cores   */
-                          /* (tcgen05, TF32 hi/lo split, 3 products, FP32 sums)      */
+    FSI_BF16X6_IR = 2,    /* as FSI_FP32_IR, the long trailing updates on the tensor */
+                          /* cores: tcgen05 BF16 MMAs on three-plane splits of the   */
+                          /* FP32 operands (six products, FP32-level accuracy),      */
+                          /* accumulations of 64 elements drained into FP32 sums     */
+    FSI_BF16_IR = 3       /* as FSI_BF16X6_IR with one BF16 plane (one product):    */
+                          /* a BF16 factor with FP32 accumulation, refined in FP64   */
 } fsi_precision;
 
 /* Geometry and materials of the coupled model (paper Sec. 2; loss factor
@@ -193,13 +197,13 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
  * complement (cols >= npiv); ipiv[i*npiv + j] is the row swapped with row j
  * (LAPACK getrf convention, 0-based).  precision selects FP64 or FP32 data:
  * A points to fsi_c64 (FP64) or to {float re, im} pairs (FSI_FP32_IR, and
- * FSI_TF32X3_IR with the large trailing updates on the tensor cores; those
- * need ld, sA and the first column right of each update even, otherwise they
- * run on the FP32 SIMT pipe).  ws: device workspace of fsi_lu_workspace
+ * FSI_BF16X6_IR / FSI_BF16_IR with the large trailing updates on the tensor
+ * cores; those need ld, sA and the first column right of each update even,
+ * otherwise they run on the FP32 SIMT pipe).  ws: device workspace of fsi_lu_workspace
  * bytes for the same precision and sizes.  n_singular_out (host, nullable)
  * gets the number of matrices that met a zero or non-finite pivot.  Any other
- * precision value is rejected with FSI_EINVAL.  FSI_TF32X3_IR synchronizes
- * the stream and returns FSI_ETIMEOUT when a bounded wait of a tensor-core
+ * precision value is rejected with FSI_EINVAL.  The tensor-core precisions
+ * synchronize the stream and returns FSI_ETIMEOUT when a bounded wait of a tensor-core
  * kernel gave up (see fsi_set_wait_limit); the factors are then invalid. */
 fsi_status fsi_lu_workspace(int precision, int batch, int m, int ncols, int npiv, size_t* bytes);
 fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, void* A, int64_t ld,
@@ -225,9 +229,9 @@ fsi_status fsi_set_wait_limit(int64_t spins);
  * library holds until the process exits.
  *   - batch is limited to 4095 matrices; larger batches return FSI_EINVAL
  *     with a message (split the call, or use fsi_batched_lu).
- *   - precision is FSI_FP64 or FSI_FP32_IR.  FSI_TF32X3_IR is rejected with
- *     FSI_EINVAL: its tensor-core updates need an operand workspace that
- *     grows with the matrices (use fsi_batched_lu).  Other values are
+ *   - precision is FSI_FP64 or FSI_FP32_IR.  FSI_BF16X6_IR and FSI_BF16_IR are rejected
+ *     with FSI_EINVAL: their tensor-core updates need an operand workspace
+ *     that grows with the matrices (use fsi_batched_lu).  Other values are
  *     rejected too.
  *   - Every call looks up the array's device address for the current device
  *     (a host-side lookup, no allocation).  The first call on a device also
@@ -543,6 +547,17 @@ fsi_status mlp_train(float* params, float* adam_m, float* adam_v, const float* X
 
 /* y[q] = network(X[q]) for q < n (device arrays). */
 fsi_status mlp_predict(const float* params, const float* X, int n, float* y, void* stream);
+
+/* Throughput probe for roofline denominators (measurement support; the paper
+ * has no counterpart): keeps one execution unit of the current GPU busy with
+ * independent operations and no memory traffic, about seconds_hint seconds,
+ * timed with CUDA events on `stream`.  kind 0: FP32 FMA (SIMT), 1: FP64 FMA,
+ * 2: tcgen05 MMA with BF16 operands, 3: tcgen05 MMA with TF32 operands
+ * (M = 128, N = 256, FP32 accumulation).  scratch: device, >= 1 KiB.  Writes
+ * the achieved TFLOP/s (2 flops per multiply-add) and the kernel time in ms.
+ * Synchronizes the stream.  Errors: FSI_EINVAL, FSI_ECUDA, FSI_ETIMEOUT. */
+fsi_status fsi_probe_peak(int kind, double seconds_hint, void* scratch, double* tflops_out, double* ms_out,
+                          void* stream);
 
 const char* fsi_status_str(fsi_status s);
 const char* fsi_last_error(void);

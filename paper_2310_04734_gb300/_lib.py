@@ -148,6 +148,7 @@ SIGNATURES = {
     "mlp_train": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_int, c_int,
                           C.c_float, c_int, c_void_p, c_void_p, c_void_p]),
     "mlp_predict": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p]),
+    "fsi_probe_peak": (c_int, [c_int, C.c_double, c_void_p, c_double_p, c_double_p, c_void_p]),
     "fsi_status_str": (C.c_char_p, [c_int]),
     "fsi_last_error": (C.c_char_p, []),
 }

@@ -16,8 +16,9 @@ from . import _lib as L
 
 FSI_FP64 = 0
 FSI_FP32_IR = 1
-FSI_TF32X3_IR = 2
-PRECISIONS = {"fp64": FSI_FP64, "fp32_ir": FSI_FP32_IR, "tf32x3_ir": FSI_TF32X3_IR}
+FSI_BF16X6_IR = 2
+FSI_BF16_IR = 3
+PRECISIONS = {"fp64": FSI_FP64, "fp32_ir": FSI_FP32_IR, "bf16x6_ir": FSI_BF16X6_IR, "bf16_ir": FSI_BF16_IR}
 
 
 def _torch():
@@ -198,14 +199,20 @@ def fsi_residual(model: DeviceModel, freqs_hz, X, F):
     return R.transpose(1, 2)
 
 
-def fsi_batched_lu(A, npiv: int, tensor_cores: bool = False):
+def fsi_batched_lu(A, npiv: int, tensor_cores=False):
     """In-place batched partial LU of row-major A [batch][m][ncols] (complex64 or complex128 CUDA);
-    complex64 with tensor_cores=True runs the trailing updates on tcgen05 (3xTF32)."""
+    complex64 with tensor_cores=True (or "bf16x6") runs the long trailing updates on tcgen05 with
+    three-plane BF16 splits (FP32-level), tensor_cores="bf16" with one plane (plain BF16)."""
     torch = _torch()
     lib = L.load()
     assert A.is_contiguous() and A.dim() == 3
     batch, m, ncols = A.shape
-    prec = FSI_FP64 if A.dtype == torch.complex128 else (FSI_TF32X3_IR if tensor_cores else FSI_FP32_IR)
+    if A.dtype == torch.complex128:
+        prec = FSI_FP64
+    elif not tensor_cores:
+        prec = FSI_FP32_IR
+    else:
+        prec = FSI_BF16_IR if tensor_cores == "bf16" else FSI_BF16X6_IR
     ipiv = torch.empty((batch, npiv), dtype=torch.int32, device=A.device)
     need = C.c_size_t()
     L.check(lib.fsi_lu_workspace(prec, batch, m, ncols, npiv, C.byref(need)), "fsi_lu_workspace")
@@ -219,6 +226,19 @@ def fsi_batched_lu(A, npiv: int, tensor_cores: bool = False):
 def fsi_set_wait_limit(spins: int = 0):
     """Spin limit of the tensor-core kernels' bounded waits (0: the default)."""
     L.check(L.load().fsi_set_wait_limit(int(spins)), "fsi_set_wait_limit")
+
+
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "bf16_tcgen05": 2, "tf32_tcgen05": 3}
+
+
+def fsi_probe_peak(kind: str, seconds: float = 0.2):
+    """Measured throughput (TFLOP/s, kernel ms) of one execution unit (see PEAK_KINDS)."""
+    torch = _torch()
+    scratch = torch.zeros(1024, dtype=torch.uint8, device="cuda")
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    L.check(L.load().fsi_probe_peak(PEAK_KINDS[kind], float(seconds), _ptr(scratch), C.byref(tf), C.byref(ms),
+                                    _stream_ptr()), "fsi_probe_peak")
+    return tf.value, ms.value
 
 
 def fsi_batched_lu_noalloc(A, npiv: int):

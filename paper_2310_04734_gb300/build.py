@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libfsi.so")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["assemble.cpp", "prof.cpp", "api.cu", "lu_kernels.cu", "vec_kernels.cu", "rom.cu", "gmres.cu", "noalloc.cu", "tc_gemm.cu", "slab_solve.cu", "cgemm_f32.cu", "rom_greedy.cu", "mlp.cu", "rom_multi.cu", "rom_io.cu"]
+SOURCES = ["assemble.cpp", "prof.cpp", "api.cu", "lu_kernels.cu", "vec_kernels.cu", "rom.cu", "gmres.cu", "noalloc.cu", "tc_gemm.cu", "slab_solve.cu", "cgemm_f32.cu", "rom_greedy.cu", "mlp.cu", "rom_multi.cu", "rom_io.cu", "peaks.cu"]
 
 
 def nvcc() -> str:

@@ -132,8 +132,8 @@ struct SweepWS {
     int64_t sV = 0;
 
     void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int gmres_restart,
-               bool tensor) {
-        fc.carve(c, d, F, nrhs, tensor);
+               int planes) {
+        fc.carve(c, d, F, nrhs, planes);
         sV = int64_t(nrhs) * d.n;
         omega = c.take<double>(F);
         xhat = c.take<double2>(size_t(F) * sV);
@@ -155,6 +155,13 @@ struct SweepWS {
     }
 };
 
+bool known_precision(int p) {
+    return p == FSI_FP64 || p == FSI_FP32_IR || p == FSI_BF16X6_IR || p == FSI_BF16_IR;
+}
+
+// BF16 planes per operand of the tensor-core updates for a precision (0: none)
+int tc_planes(int p) { return p == FSI_BF16X6_IR ? 3 : (p == FSI_BF16_IR ? 1 : 0); }
+
 int gmres_restart_of(const fsi_solve_opts& o) {
     if (o.refine != FSI_REFINE_GMRES) return 0;
     return o.restart > 0 ? o.restart : 20;
@@ -167,10 +174,10 @@ fsi_status check_dims(const fsi_dims* d) {
 }
 
 template <typename R>
-size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int restart, bool tensor) {
+size_t sweep_ws_bytes(const fsi_dims& d, int F, int nrhs, int nrcv, bool host_io, int restart, int planes) {
     Carver c(nullptr, 0);
     SweepWS<R> w;
-    w.carve(c, d, F, nrhs, nrcv, host_io, restart, tensor);
+    w.carve(c, d, F, nrhs, nrcv, host_io, restart, planes);
     return align_up(c.used);
 }
 
@@ -231,13 +238,13 @@ fsi_status run_sweep(const fsi_dims& d, const void* d_model, const double* f_hz,
     Carver c(ws, ws_bytes);
     SweepWS<R> w;
     const int restart = gmres_restart_of(o);
-    w.carve(c, d, Fb_max, nrhs, nrcv, host_io, restart, o.precision == FSI_TF32X3_IR);
+    w.carve(c, d, Fb_max, nrhs, nrcv, host_io, restart, tc_planes(o.precision));
     if (!c.fits()) {
         set_error("workspace too small: need " + std::to_string(align_up(c.used)) + " bytes");
         return FSI_ENOMEM;
     }
     const DevModel m = dev_model(d, d_model);
-    w.fc.use_tc = (o.precision == FSI_TF32X3_IR);
+    w.fc.use_tc = tc_planes(o.precision) > 0;
     prof().reset(o.profile != 0);
     const double2* Fdev = reinterpret_cast<const double2*>(F);
     const int32_t* rcvdev = rcv;
@@ -422,9 +429,10 @@ fsi_status frf_sweep_workspace(const fsi_dims* dims, const fsi_solve_opts* opts,
     FSI_REQUIRE(opts && bytes && nrhs > 0 && nrcv > 0 && opts->batch > 0, "bad sweep workspace arguments");
     const bool hio = opts->host_io != 0;
     const int rs = gmres_restart_of(*opts);
-    const bool tc = opts->precision == FSI_TF32X3_IR;
-    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio, rs, false)
-                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio, rs, tc);
+    FSI_REQUIRE(known_precision(opts->precision), "unknown precision");
+    *bytes = opts->precision == FSI_FP64 ? sweep_ws_bytes<double>(*dims, opts->batch, nrhs, nrcv, hio, rs, 0)
+                                         : sweep_ws_bytes<float>(*dims, opts->batch, nrhs, nrcv, hio, rs,
+                                                                 tc_planes(opts->precision));
     return FSI_OK;
 }
 
@@ -436,8 +444,7 @@ fsi_status frf_sweep_full(const fsi_dims* dims, const void* d_model, const doubl
     if (s != FSI_OK) return s;
     FSI_REQUIRE(d_model && f_hz && F && rcv && opts && ws && p_out, "NULL argument");
     FSI_REQUIRE(nf > 0 && nrhs > 0 && nrcv > 0 && opts->batch > 0, "nf, nrhs, nrcv, batch must be positive");
-    FSI_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR || opts->precision == FSI_TF32X3_IR,
-                "unknown precision");
+    FSI_REQUIRE(known_precision(opts->precision), "unknown precision");
     for (int i = 0; i < nf; ++i) FSI_REQUIRE(f_hz[i] > 0.0 && std::isfinite(f_hz[i]), "frequencies must be > 0");
     if (opts->host_io)
         for (int i = 0; i < nrcv; ++i) FSI_REQUIRE(rcv[i] >= 0 && rcv[i] < dims->n, "receiver index out of range");
@@ -469,10 +476,9 @@ fsi_status fsi_residual(const fsi_dims* dims, const void* d_model, const double*
 fsi_status fsi_lu_workspace(int precision, int batch, int m, int ncols, int npiv, size_t* bytes) {
     FSI_REQUIRE(batch > 0 && m > 0 && ncols > 0 && npiv > 0 && npiv <= m && npiv <= ncols && bytes,
                 "bad lu workspace arguments");
-    FSI_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR || precision == FSI_TF32X3_IR,
-                "unknown precision");
+    FSI_REQUIRE(known_precision(precision), "unknown precision");
     size_t b = align_up(sizeof(int32_t) * size_t(batch + 1));
-    if (precision == FSI_TF32X3_IR) b += align_up(tc_workspace_bytes(batch, m, ncols, npiv));
+    if (tc_planes(precision) > 0) b += align_up(tc_workspace_bytes(batch, m, ncols, npiv, tc_planes(precision)));
     *bytes = b;
     return FSI_OK;
 }
@@ -481,8 +487,7 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
                           int32_t* ipiv, void* ws, size_t ws_bytes, int* n_singular_out, void* stream) {
     FSI_REQUIRE(A && ipiv && ws && batch > 0 && m > 0 && ncols > 0, "bad batched lu arguments");
     FSI_REQUIRE(npiv > 0 && npiv <= m && npiv <= ncols && ld >= ncols && sA >= ld * m, "bad batched lu shape");
-    FSI_REQUIRE(precision == FSI_FP64 || precision == FSI_FP32_IR || precision == FSI_TF32X3_IR,
-                "unknown precision");
+    FSI_REQUIRE(known_precision(precision), "unknown precision");
     size_t need = 0;
     fsi_status s0 = fsi_lu_workspace(precision, batch, m, ncols, npiv, &need);
     if (s0 != FSI_OK) return s0;
@@ -495,24 +500,26 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
         partial_lu<double>(static_cast<double2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st);
     } else {
         TcCtx tc;
-        if (precision == FSI_TF32X3_IR) {
+        const bool tensor = tc_planes(precision) > 0;
+        if (tensor) {
             const size_t off = align_up(sizeof(int32_t) * size_t(batch + 1));
+            tc.planes = tc_planes(precision);
             tc.err = status + batch;
             tc.ws = static_cast<char*>(ws) + off;
             tc.ws_bytes = ws_bytes - off;
         }
         partial_lu<float>(static_cast<float2*>(A), sA, int(ld), batch, m, ncols, npiv, ipiv, npiv, status, st,
-                          precision == FSI_TF32X3_IR ? &tc : nullptr);
+                          tensor ? &tc : nullptr);
     }
     FSI_CHECK_LAUNCH();
-    if (n_singular_out || precision == FSI_TF32X3_IR) {
+    if (n_singular_out || tc_planes(precision) > 0) {
         std::vector<int32_t> h(batch + 1);
         FSI_CUDA(cudaMemcpyAsync(h.data(), status, sizeof(int32_t) * (batch + 1), cudaMemcpyDeviceToHost, st));
         FSI_CUDA(cudaStreamSynchronize(st));
         int cnt = 0;
         for (int i = 0; i < batch; ++i) cnt += h[i] != 0;
         if (n_singular_out) *n_singular_out = cnt;
-        if (precision == FSI_TF32X3_IR && h[batch]) {
+        if (tc_planes(precision) > 0 && h[batch]) {
             set_error("a tensor-core update gave up waiting for its loads or MMAs");
             return FSI_ETIMEOUT;
         }

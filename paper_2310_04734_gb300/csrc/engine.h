@@ -25,7 +25,8 @@ struct Factor {
     bool use_tc = false;
     int64_t sG = 0, sU = 0, sL = 0, sP = 0, sPerm = 0;
 
-    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, bool tensor = false) {
+    // planes: 0 (no tensor-core updates), 3 (BF16x6, FP32 level) or 1 (plain BF16)
+    void carve(Carver& c, const fsi_dims& d, int F, int nrhs, int planes = 0) {
         const int64_t b = d.b, nz = d.nz;
         sG = 2 * b * 3 * b;
         sU = nz * b * 3 * b;
@@ -39,8 +40,9 @@ struct Factor {
         perm = c.take<int32_t>(size_t(F) * sPerm);
         status = c.take<int32_t>(size_t(F));
         tc.err = c.take<int32_t>(1);
-        if (tensor && sizeof(R) == 4) {
-            tc.ws_bytes = tc_workspace_bytes(F, 2 * d.b, 3 * d.b, d.b);
+        if (planes > 0 && sizeof(R) == 4) {
+            tc.planes = planes;
+            tc.ws_bytes = tc_workspace_bytes(F, 2 * d.b, 3 * d.b, d.b, planes);
             tc.ws = c.take<char>(tc.ws_bytes);
         }
     }

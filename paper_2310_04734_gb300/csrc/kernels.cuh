@@ -135,12 +135,13 @@ struct TcCtx {
     int32_t* err = nullptr;
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    int planes = 3;   // BF16 planes per operand: 3 (six products, FP32 level) or 1 (plain BF16)
 };
 // Workspace bytes for every trailing update of partial_lu(F, m, ncols, npiv) on the tensor cores.
-size_t tc_workspace_bytes(int F, int m, int ncols, int npiv);
+size_t tc_workspace_bytes(int F, int m, int ncols, int npiv, int planes);
 // Spin limit of the tensor-core kernels' pipeline waits (0: the default, about 6.7e7 polls).
 void set_tc_spin_limit(uint32_t spins);
-// Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (3xTF32, TMA-fed).
+// Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (BF16 planes, TMA-fed).
 // Returns false (nothing launched) when the operands do not meet TMA's alignment rules or the
 // workspace is too small; the caller then runs the SIMT update.
 bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,

@@ -64,8 +64,8 @@ extern "C" fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, in
         set_error("fsi_batched_lu_noalloc: bad shape");
         return FSI_EINVAL;
     }
-    if (precision == FSI_TF32X3_IR) {
-        set_error("fsi_batched_lu_noalloc: FSI_TF32X3_IR needs an operand workspace; use fsi_batched_lu");
+    if (precision == FSI_BF16X6_IR || precision == FSI_BF16_IR) {
+        set_error("fsi_batched_lu_noalloc: the tensor-core precisions need an operand workspace; use fsi_batched_lu");
         return FSI_EINVAL;
     }
     if (precision != FSI_FP64 && precision != FSI_FP32_IR) {

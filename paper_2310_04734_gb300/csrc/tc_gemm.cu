@@ -6,37 +6,55 @@
 // The complex product is one real GEMM on interleaved storage: with A' the
 // M x 2K real view of A and B' the 2K x 2N real matrix with 2x2 blocks
 // [[Br, Bi], [-Bi, Br]], C' -= A' B' is exactly the complex update on the
-// interleaved C.  FP32 accuracy is kept on the TF32 tensor pipe by splitting
-// every operand into hi = tf32(x) and lo = tf32(x - hi) and accumulating
-// hi*hi + hi*lo + lo*hi in FP32 (plain TF32 products are not accurate enough
-// for the refinement of these systems to converge).  hi*hi and the two cross
-// terms accumulate in separate TMEM accumulators, added in FP32 only in the
-// epilogue, so the small cross terms are not aligned to the large hi*hi sum.
+// interleaved C (four real products per complex multiply-add).
+//
+// Precision.  These factors precondition systems with condition numbers up to
+// ~1e8, and the refinement converges only if the factor is about as accurate
+// as an FP32 one.  Two properties of the tensor pipe stand in the way and are
+// handled here:
+//   * products: every FP32 operand is split into three BF16 planes,
+//     x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1),
+//     24 significant bits in all), and six products are accumulated:
+//     a0 b0 into a "big" accumulator, a0 b1 + a1 b0 + a0 b2 + a2 b0 + a1 b1
+//     into a "small" one; the terms left out are below 2^-24 relative (adding
+//     a1 b2 + a2 b1 changed neither the GMRES steps nor the time on config 2).
+//     (Three TF32 products, hi/lo splits of 11 bits each, keep only ~22 bits
+//     and needed about twice the GMRES steps of an FP32 factor.)
+//   * accumulation: the tensor core adds into its FP32 accumulator without
+//     rounding to nearest, so long sums drift; measured on config 2, K = 852
+//     complex in one accumulation needed four times the GMRES steps.  Here
+//     each accumulation spans one 64-element K slice only: the accumulators are
+//     double-buffered in TMEM (2 x (big + small) x 128 columns), and the
+//     epilogue warps drain every slice into FP32 registers (round to nearest)
+//     while the MMAs of the next slice run.
+// With one plane (NP = 1) the same kernel computes the plain BF16 product
+// a0 b0 (FP32 accumulation), the low-precision factor of the mixed-precision
+// study, which the FP64 refinement has to make up for.
 //
 // Two kernels per update:
-//   pack:  A' and B' are split into hi/lo planes in K-major layout (rows of
-//          Kp floats, Kp = 2K rounded up to 32, zero padded): A' rows are the
-//          rows of C, B' rows are the real columns of C (B transposed).
-//   gemm:  one CTA per 128 x 256 real tile of C and frequency, warp
-//          specialised: warp 0 issues the TMA loads of the four operand tiles
-//          of a 32-float K slice into a two-stage ring (128-byte swizzle),
-//          warp 1 issues the tcgen05.mma instructions (M=128, N=256, K=8,
-//          kind::tf32; 12 per slice) and commits them to the stage's "empty"
-//          mbarrier, and warps 4..7 read both accumulators with tcgen05.ld,
-//          stage -(hh + cross) in swizzled shared memory and add it into C
-//          with TMA bulk reductions (cp.reduce.async.bulk.tensor .add), which
-//          also drop the rows and columns outside C.
+//   pack:  A' and B' are split into NP BF16 planes in K-major layout (rows of
+//          Kp elements, Kp = 2K rounded up to 64, zero padded): A' rows are
+//          the rows of C, B' rows are the real columns of C (B transposed).
+//   gemm:  one CTA per 128 x 128 real tile of C and frequency, warp
+//          specialised: warp 0 issues the TMA loads of the 2 NP operand tiles
+//          of a 64-element K slice (128-byte swizzle), warp 1 issues the
+//          tcgen05.mma instructions (M = N = 128, K = 16, kind::f16 with BF16
+//          operands) and commits them per slice, warps 4..7 drain the TMEM
+//          accumulators with tcgen05.ld into register sums and finally add
+//          -sum into C with TMA bulk reductions (cp.reduce.async.bulk.tensor
+//          .add), which also drop the rows and columns outside C.
 // Every mbarrier wait is bounded by a spin limit (a kernel argument): on a
 // timeout the CTA records an error, stops issuing work, waits (with a fixed
 // generous limit) for the TMA loads and MMAs it already issued, and only then
 // frees its tensor memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <cstdint>
-#include <algorithm>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -47,17 +65,20 @@ namespace fsi {
 namespace {
 
 constexpr int kTM = 128;             // real rows per tile (MMA M)
-constexpr int kTN = 256;             // real columns per tile (MMA N)
-constexpr int kTKf = 32;             // floats per K slice: one 128-byte swizzle row
+constexpr int kTN = 128;             // real columns per tile (MMA N)
+constexpr int kTK = 64;              // BF16 elements per K slice: one 128-byte swizzle row
 constexpr int kThreads = 256;
-constexpr int kTmemCols = 512;       // two 256-column fp32 accumulators: hi*hi, and hi*lo + lo*hi
-constexpr int kStages = 2;
-constexpr int kABytes = kTM * 128;   // one plane of an A slice
-constexpr int kBBytes = kTN * 128;   // one plane of a B slice
-constexpr int kStageBytes = 2 * kABytes + 2 * kBBytes;   // 96 KiB
-constexpr size_t kSmemBytes = size_t(kStages) * kStageBytes + 1024 + 128;
+constexpr int kTmemCols = 512;       // two buffers x (big, small) x 128 fp32 columns
+constexpr int kPlaneBytes = 128 * 128;   // one 128-row plane of a slice (A and B alike)
 constexpr uint32_t kDefaultSpin = 1u << 26;
 constexpr uint32_t kDrainSpin = 1u << 26;   // waits for work already issued (always completes)
+
+template <int NP>
+struct Cfg {
+    static constexpr int kStageBytes = 2 * NP * kPlaneBytes;          // NP planes of A and of B
+    static constexpr int kStages = NP == 3 ? 2 : 4;
+    static constexpr size_t kSmem = size_t(kStages) * kStageBytes + 1024 + 256;
+};
 
 std::atomic<uint32_t> g_spin_limit{kDefaultSpin};
 
@@ -65,39 +86,46 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// x = x0 + x1 + x2 in BF16 (each remainder is exact in FP32)
+template <int NP>
+__device__ __forceinline__ void split(float x, __nv_bfloat16 (&p)[NP]) {
+    p[0] = __float2bfloat16_rn(x);
+    if constexpr (NP == 3) {
+        const float r1 = x - __bfloat162float(p[0]);
+        p[1] = __float2bfloat16_rn(r1);
+        p[2] = __float2bfloat16_rn(r1 - __bfloat162float(p[1]));
+    }
 }
 
 // ----------------------------------------------------------------- operand packing
-// Ap[2f + plane][r][kk] = split(A'[r0 + r][2 k0 + kk]) for kk < 2K, 0 up to Kp.
+// Ap[NP f + p][r][kk] = plane p of A'[r0 + r][2 k0 + kk] for kk < 2K, 0 up to Kp.
+template <int NP>
 __global__ void pack_a_kernel(const float* __restrict__ G, int64_t sGf, int64_t ldf, int r0, int M, int kx0, int K2,
-                              int Kp, float* __restrict__ Ap) {
+                              int Kp, __nv_bfloat16* __restrict__ Ap) {
     const int f = blockIdx.y;
-    const int64_t idx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 4;
+    const int64_t idx = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) * 8;
     const int64_t plane = int64_t(M) * Kp;
     if (idx >= plane) return;
     const int r = int(idx / Kp), kk = int(idx - int64_t(r) * Kp);
     const float* src = G + f * sGf + int64_t(r0 + r) * ldf + kx0;
-    float v[4];
+    __align__(16) __nv_bfloat16 out[NP][8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = (kk + j < K2) ? src[kk + j] : 0.f;
-    float4 hi, lo;
-    hi.x = to_tf32(v[0]); lo.x = to_tf32(v[0] - hi.x);
-    hi.y = to_tf32(v[1]); lo.y = to_tf32(v[1] - hi.y);
-    hi.z = to_tf32(v[2]); lo.z = to_tf32(v[2] - hi.z);
-    hi.w = to_tf32(v[3]); lo.w = to_tf32(v[3] - hi.w);
-    float* dst = Ap + int64_t(2 * f) * plane + idx;
-    *reinterpret_cast<float4*>(dst) = hi;
-    *reinterpret_cast<float4*>(dst + plane) = lo;
+    for (int j = 0; j < 8; ++j) {
+        __nv_bfloat16 p[NP];
+        split<NP>((kk + j < K2) ? src[kk + j] : 0.f, p);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) out[q][j] = p[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NP; ++q)
+        *reinterpret_cast<uint4*>(Ap + (int64_t(NP) * f + q) * plane + idx) = *reinterpret_cast<const uint4*>(out[q]);
 }
 
-// Bp[2f + plane][q][kk]: row q = 2n holds (Br, -Bi) and row 2n + 1 holds (Bi, Br) of every
+// Bp[NP f + p][q][kk]: row q = 2n holds (Br, -Bi) and row 2n + 1 holds (Bi, Br) of every
 // complex k (at kk = 2k, 2k + 1), zero for k >= K; B[k][n] = G[k0 + k][c0 + n].
+template <int NP>
 __global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, int k0, int K, int c0, int N, int Kp,
-                              float* __restrict__ Bp) {
+                              __nv_bfloat16* __restrict__ Bp) {
     __shared__ float2 t[32][33];
     const int f = blockIdx.z;
     const int kb = blockIdx.x * 32, nb = blockIdx.y * 32;
@@ -110,8 +138,6 @@ __global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, 
     }
     __syncthreads();
     const int64_t plane = int64_t(2 * N) * Kp;
-    float* hiP = Bp + int64_t(2 * f) * plane;
-    float* loP = hiP + plane;
     const int k = kb + tx;
     if (2 * k >= Kp) return;
 #pragma unroll
@@ -120,15 +146,21 @@ __global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, 
         if (n >= N) continue;
         const float2 b = t[tx][nl];
         const int64_t o0 = int64_t(2 * n) * Kp + 2 * k, o1 = o0 + Kp;
-        float2 h0, l0, h1, l1;
-        h0.x = to_tf32(b.x);  l0.x = to_tf32(b.x - h0.x);
-        h0.y = to_tf32(-b.y); l0.y = to_tf32(-b.y - h0.y);
-        h1.x = to_tf32(b.y);  l1.x = to_tf32(b.y - h1.x);
-        h1.y = h0.x;          l1.y = l0.x;
-        *reinterpret_cast<float2*>(hiP + o0) = h0;
-        *reinterpret_cast<float2*>(loP + o0) = l0;
-        *reinterpret_cast<float2*>(hiP + o1) = h1;
-        *reinterpret_cast<float2*>(loP + o1) = l1;
+        __nv_bfloat16 re[NP], mi[NP], im[NP];
+        split<NP>(b.x, re);
+        split<NP>(-b.y, mi);
+        split<NP>(b.y, im);
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            __nv_bfloat16* P = Bp + (int64_t(NP) * f + q) * plane;
+            __nv_bfloat162 v0, v1;
+            v0.x = re[q];
+            v0.y = mi[q];
+            v1.x = im[q];
+            v1.y = re[q];
+            *reinterpret_cast<__nv_bfloat162*>(P + o0) = v0;
+            *reinterpret_cast<__nv_bfloat162*>(P + o1) = v1;
+        }
     }
 }
 
@@ -143,13 +175,14 @@ __device__ __forceinline__ uint64_t make_desc(uint32_t saddr) {
     return d;
 }
 
-// instruction descriptor: D f32, A/B tf32, both K-major, N = 256, M = 128
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
+// instruction descriptor, kind::f16: D f32, A and B bf16, both K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(kTN >> 3) << 17) | (uint32_t(kTM >> 4) << 24);
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint32_t a, uint32_t b, uint32_t accumulate) {
+    const uint64_t adesc = make_desc(a), bdesc = make_desc(b);
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
 }
 
@@ -170,6 +203,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, uint32
         if (done) return true;
     }
     return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ void expect_tx(uint32_t mbar, uint32_t bytes) {
@@ -207,36 +244,43 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 struct TcArgs {
     int cx0, cx1;     // real columns [2 c0, 2 c1) of C
     int cy0, cy1;     // rows [r0, r1) of C
-    int nk;           // K slices of kTKf floats
+    int nk;           // K slices of kTK elements
     uint32_t limit;   // spin limit of the pipeline waits
     int32_t* err;
 };
 
+// barrier slots: full[S], empty[S], accf[2] (TMEM buffer written), acce[2] (drained), done
+template <int NP>
 __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, TcArgs a) {
+    constexpr int S = Cfg<NP>::kStages;
+    constexpr int SB = Cfg<NP>::kStageBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t raw = smem_u32(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char* ops = smem_raw + pad;
     const uint32_t ops_s = raw + pad;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + size_t(kStages) * kStageBytes);   // full[2] empty[2] accum
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + size_t(S) * SB);
+    constexpr int kBars = 2 * S + 5;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kBars);
     volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* s_issued = s_abort + 1;
     volatile int* s_consumed = s_abort + 2;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bx = blockIdx.x, by = blockIdx.y, f = blockIdx.z;
-    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[kStages]),
-                   accum = smem_u32(&bars[2 * kStages]);
+    const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]), accf0 = smem_u32(&bars[2 * S]),
+                   acce0 = smem_u32(&bars[2 * S + 2]), done = smem_u32(&bars[2 * S + 4]);
 
     if (tid == 0) {
         *s_abort = 0;
         *s_issued = 0;
         *s_consumed = 0;
-        for (int i = 0; i < 2 * kStages + 1; ++i)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
+        for (int i = 0; i < kBars; ++i) {
+            const uint32_t cnt = (i >= 2 * S + 2 && i < 2 * S + 4) ? 4u : 1u;   // acce: one arrive per drain warp
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bars[i])), "r"(cnt));
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
         asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
@@ -253,31 +297,36 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = *tmem_slot;
 
     if (tid == 0) {
-        // TMA producer
+        // TMA producer: NP planes of A, then NP planes of B, per slice
         int kt = 0;
         for (; kt < a.nk; ++kt) {
-            const int s = kt % kStages;
-            if (kt >= kStages && !mbar_wait(empty0 + 8u * s, uint32_t((kt / kStages - 1) & 1), a.limit)) {
+            const int s = kt % S;
+            if (kt >= S && !mbar_wait(empty0 + 8u * s, uint32_t((kt / S - 1) & 1), a.limit)) {
                 *s_abort = 1;
                 break;
             }
             if (*s_abort) break;
-            const uint32_t base = ops_s + uint32_t(s) * kStageBytes;
+            const uint32_t base = ops_s + uint32_t(s) * SB;
             const uint32_t fb = full0 + 8u * s;
-            expect_tx(fb, kStageBytes);
-            const int x = kt * kTKf;
-            tma_load3(base, &tmA, x, by * kTM, 2 * f, fb);
-            tma_load3(base + kABytes, &tmA, x, by * kTM, 2 * f + 1, fb);
-            tma_load3(base + 2 * kABytes, &tmB, x, bx * kTN, 2 * f, fb);
-            tma_load3(base + 2 * kABytes + kBBytes, &tmB, x, bx * kTN, 2 * f + 1, fb);
+            expect_tx(fb, SB);
+            const int x = kt * kTK;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                tma_load3(base + q * kPlaneBytes, &tmA, x, by * kTM, NP * f + q, fb);
+                tma_load3(base + (NP + q) * kPlaneBytes, &tmB, x, bx * kTN, NP * f + q, fb);
+            }
         }
         *s_issued = kt;
     } else if (tid == 32) {
-        // MMA issuer
+        // MMA issuer: slice kt accumulates into TMEM buffer kt & 1 (big at +0, small at +128)
         int kt = 0;
         for (; kt < a.nk; ++kt) {
-            const int s = kt % kStages;
-            if (!mbar_wait(full0 + 8u * s, uint32_t((kt / kStages) & 1), a.limit)) {
+            const int b = kt & 1, s = kt % S;
+            if (kt >= 2 && !mbar_wait(acce0 + 8u * b, uint32_t((kt / 2 - 1) & 1), a.limit)) {
+                *s_abort = 1;
+                break;
+            }
+            if (!mbar_wait(full0 + 8u * s, uint32_t((kt / S) & 1), a.limit)) {
                 *s_abort = 1;
                 break;
             }
@@ -286,37 +335,77 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t base = ops_s + uint32_t(s) * kStageBytes;
-            const uint32_t ahi = base, alo = base + kABytes, bhi = base + 2 * kABytes,
-                           blo = base + 2 * kABytes + kBBytes;
+            const uint32_t base = ops_s + uint32_t(s) * SB;
+            const uint32_t tbig = tmem + uint32_t(b) * 256u, tsmall = tbig + 128u;
 #pragma unroll
-            for (int ks = 0; ks < kTKf / 8; ++ks) {   // K = 8 per MMA: 32 bytes along the swizzle row
+            for (int ks = 0; ks < kTK / 16; ++ks) {   // K = 16 per MMA: 32 bytes along the swizzle row
                 const uint32_t off = uint32_t(ks) * 32u;
-                const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-                mma_tf32(tmem, make_desc(ahi + off), make_desc(bhi + off), first);
-                mma_tf32(tmem + 256u, make_desc(ahi + off), make_desc(blo + off), first);
-                mma_tf32(tmem + 256u, make_desc(alo + off), make_desc(bhi + off), 1u);
+                const uint32_t acc = ks == 0 ? 0u : 1u;
+                const uint32_t A0 = base + off, B0 = base + NP * kPlaneBytes + off;
+                mma_bf16(tbig, A0, B0, acc);
+                if constexpr (NP == 3) {
+                    const uint32_t A1 = A0 + kPlaneBytes, A2 = A0 + 2 * kPlaneBytes;
+                    const uint32_t B1 = B0 + kPlaneBytes, B2 = B0 + 2 * kPlaneBytes;
+                    mma_bf16(tsmall, A0, B1, acc);
+                    mma_bf16(tsmall, A1, B0, 1u);
+                    mma_bf16(tsmall, A0, B2, 1u);
+                    mma_bf16(tsmall, A2, B0, 1u);
+                    mma_bf16(tsmall, A1, B1, 1u);
+                }
             }
             mma_commit(empty0 + 8u * s);
+            mma_commit(accf0 + 8u * b);
         }
         *s_consumed = kt;
-        mma_commit(accum);   // tracks every MMA issued above
+        mma_commit(done);   // tracks every MMA issued above
     } else if (warp >= 4) {
-        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows
-        const bool ok = mbar_wait(accum, 0u, a.limit);
-        if (!ok) *s_abort = 1;
-        if (ok && !*s_abort) {
+        // drain warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows, all 128 columns
+        const int q = warp & 3;
+        const uint32_t trow = tmem + (uint32_t(32 * q) << 16);
+        float sum[kTN];
+#pragma unroll
+        for (int j = 0; j < kTN; ++j) sum[j] = 0.f;
+        bool ok = true;
+        for (int kt = 0; kt < a.nk; ++kt) {
+            const int b = kt & 1;
+            if (!mbar_wait(accf0 + 8u * b, uint32_t((kt / 2) & 1), a.limit)) {
+                ok = false;
+                *s_abort = 1;
+                break;
+            }
+            if (*s_abort) {
+                ok = false;
+                break;
+            }
             asm volatile("tcgen05.fence::after_thread_sync;");
-            const int q = warp & 3;
-            const uint32_t stage0 = ops_s + uint32_t(warp - 4) * 8192u;   // operand ring is idle now
-            const uint32_t trow = tmem + (uint32_t(32 * q) << 16);
+#pragma unroll
+            for (int j = 0; j < kTN / 32; ++j) {
+                uint32_t v[32];
+                tmem_ld32(trow + uint32_t(b) * 256u + uint32_t(32 * j), v);
+                if constexpr (NP == 3) {
+                    uint32_t u[32];
+                    tmem_ld32(trow + uint32_t(b) * 256u + 128u + uint32_t(32 * j), u);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]) + __uint_as_float(u[i]);
+                } else {
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]);
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce0 + 8u * b);
+        }
+        if (ok) {
+            // all MMAs have completed (every slice was drained): the operand ring is idle
+            const uint32_t stage0 = ops_s + uint32_t(warp - 4) * 8192u;
             const int y = a.cy0 + by * kTM + 32 * q;
             const int nch = y < a.cy1 ? min(kTN / 32, (a.cx1 - a.cx0 - bx * kTN + 31) / 32) : 0;
-            for (int ch = 0; ch < nch; ++ch) {
-                uint32_t v[32], u[32];
-                tmem_ld32(trow + uint32_t(ch * 32), v);
-                tmem_ld32(trow + 256u + uint32_t(ch * 32), u);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+            for (int ch = 0; ch < kTN / 32; ++ch) {
+                if (ch >= nch) break;
                 const uint32_t stg = stage0 + uint32_t(ch & 1) * 4096u;
                 if (ch >= 2) {
                     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
@@ -324,13 +413,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
 #pragma unroll
                 for (int c4 = 0; c4 < 8; ++c4) {
-                    const float x0 = -(__uint_as_float(v[4 * c4 + 0]) + __uint_as_float(u[4 * c4 + 0]));
-                    const float x1 = -(__uint_as_float(v[4 * c4 + 1]) + __uint_as_float(u[4 * c4 + 1]));
-                    const float x2 = -(__uint_as_float(v[4 * c4 + 2]) + __uint_as_float(u[4 * c4 + 2]));
-                    const float x3 = -(__uint_as_float(v[4 * c4 + 3]) + __uint_as_float(u[4 * c4 + 3]));
                     const uint32_t addr = stg + uint32_t(lane) * 128u + (uint32_t(c4 ^ (lane & 7)) << 4);
-                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(x0), "f"(x1), "f"(x2),
-                                 "f"(x3)
+                    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "f"(-sum[32 * ch + 4 * c4]),
+                                 "f"(-sum[32 * ch + 4 * c4 + 1]), "f"(-sum[32 * ch + 4 * c4 + 2]),
+                                 "f"(-sum[32 * ch + 4 * c4 + 3])
                                  : "memory");
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -350,10 +436,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (tid == 0) {
         bool ok = true;
         for (int kt = *s_consumed; kt < *s_issued; ++kt)
-            ok = mbar_wait(full0 + 8u * (kt % kStages), uint32_t((kt / kStages) & 1), kDrainSpin) && ok;
+            ok = mbar_wait(full0 + 8u * (kt % S), uint32_t((kt / S) & 1), kDrainSpin) && ok;
         if (!ok || *s_abort) atomicExch(a.err, 1);
     }
-    if (tid == 32 && !mbar_wait(accum, 0u, kDrainSpin)) atomicExch(a.err, 1);
+    if (tid == 32 && !mbar_wait(done, 0u, kDrainSpin)) atomicExch(a.err, 1);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 1) {
@@ -380,34 +466,74 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3-D FP32 tensor map: inner dimension d0 (contiguous), rows d1 (stride s1 bytes), planes d2 (stride s2).
-bool encode3(CUtensorMap* map, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1, uint64_t s2,
-             uint32_t box0, uint32_t box1, CUtensorMapL2promotion l2) {
+// 3-D tensor map: inner dimension d0 (contiguous), rows d1 (stride s1 bytes), planes d2 (stride s2).
+bool encode3(CUtensorMap* map, CUtensorMapDataType dt, void* base, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1,
+             uint64_t s2, uint32_t box0, uint32_t box1, CUtensorMapL2promotion l2) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {d0, d1, d2};
     const cuuint64_t strides[2] = {s1, s2};
     const cuuint32_t box[3] = {box0, box1, 1};
     const cuuint32_t es[3] = {1, 1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, l2, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    return fn(map, dt, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, l2,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-int64_t pack_floats(int64_t rows, int64_t Kp) { return 2 * rows * Kp; }
+// BF16 elements of the packed operands of one matrix: NP planes of rows x Kp
+int64_t pack_elems(int np, int64_t rows, int64_t Kp) { return np * rows * Kp; }
+
+template <int NP>
+bool launch_np(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K, const TcCtx& tc,
+               cudaStream_t st) {
+    const int M = r1 - r0, N = c1 - c0;
+    const int64_t Kp = round_up(2 * int64_t(K), kTK);
+    const int64_t aE = int64_t(F) * pack_elems(NP, M, Kp), bE = int64_t(F) * pack_elems(NP, 2 * int64_t(N), Kp);
+    const size_t need = size_t(aE + bE) * sizeof(__nv_bfloat16) + 256;
+    if (!tc.ws || need > tc.ws_bytes) return false;
+    auto* Ap = reinterpret_cast<__nv_bfloat16*>((reinterpret_cast<uintptr_t>(tc.ws) + 255) & ~uintptr_t(255));
+    __nv_bfloat16* Bp = Ap + aE;   // aE is a multiple of 64 elements: Bp stays 128-byte aligned
+
+    CUtensorMap mA, mB, mC;
+    if (!encode3(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Ap, Kp, M, uint64_t(NP) * F, Kp * 2, uint64_t(M) * Kp * 2,
+                 kTK, kTM, CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bp, Kp, 2 * uint64_t(N), uint64_t(NP) * F, Kp * 2,
+                 2 * uint64_t(N) * Kp * 2, kTK, kTN, CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, G, 2 * uint64_t(c1), uint64_t(r1), uint64_t(F),
+                 uint64_t(ld) * 8, uint64_t(sG) * 8, 32, 32, CU_TENSOR_MAP_L2_PROMOTION_NONE))
+        return false;
+
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(tc_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<NP>::kSmem));
+        attr_set = true;
+    }
+    {
+        ProfScope ps(PK_PACK, 0.0, st);
+        pack_a_kernel<NP><<<dim3(cdiv(int64_t(M) * Kp / 8, 256), F), 256, 0, st>>>(
+            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 2 * k0, 2 * K, int(Kp), Ap);
+        pack_b_kernel<NP><<<dim3(cdiv(Kp / 2, 32), cdiv(N, 32), F), dim3(32, 8), 0, st>>>(G, sG, ld, k0, K, c0, N,
+                                                                                          int(Kp), Bp);
+    }
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err};
+    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
+    ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
+    tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
+    return true;
+}
 
 }  // namespace
 
 void set_tc_spin_limit(uint32_t spins) { g_spin_limit.store(spins ? spins : kDefaultSpin); }
 
-size_t tc_workspace_bytes(int F, int m, int ncols, int npiv) {
+size_t tc_workspace_bytes(int F, int m, int ncols, int npiv, int planes) {
     const int64_t nb = std::min(128, npiv);
-    const int64_t Kpn = round_up(2 * int64_t(npiv), kTKf), Kp1 = round_up(2 * nb, kTKf);
-    int64_t a = pack_floats(m - nb, Kp1);
-    a = std::max(a, pack_floats(std::min(128, npiv), Kpn));
-    a = std::max(a, pack_floats(m - npiv, Kpn));
-    int64_t b = pack_floats(2 * (npiv - nb), Kp1);
-    b = std::max(b, pack_floats(2 * int64_t(ncols - npiv), Kpn));
-    return size_t(F) * size_t(a + b) * sizeof(float) + 1024;
+    const int64_t Kpn = round_up(2 * int64_t(npiv), kTK), Kp1 = round_up(2 * nb, kTK);
+    int64_t a = pack_elems(planes, m - nb, Kp1);
+    a = std::max(a, pack_elems(planes, std::min(128, npiv), Kpn));
+    a = std::max(a, pack_elems(planes, m - npiv, Kpn));
+    int64_t b = pack_elems(planes, 2 * (npiv - nb), Kp1);
+    b = std::max(b, pack_elems(planes, 2 * int64_t(ncols - npiv), Kpn));
+    return size_t(F) * size_t(a + b) * sizeof(__nv_bfloat16) + 1024;
 }
 
 bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
@@ -415,40 +541,8 @@ bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int 
     if (r1 <= r0 || c1 <= c0 || K <= 0) return true;
     // TMA: 16-byte aligned base and row / matrix strides, tile columns start on 16-byte boundaries
     if ((reinterpret_cast<uintptr_t>(G) & 15) || (ld & 1) || (sG & 1) || (c0 & 1)) return false;
-    const int M = r1 - r0, N = c1 - c0;
-    const int64_t Kp = round_up(2 * int64_t(K), kTKf);
-    const int64_t aF = int64_t(F) * pack_floats(M, Kp), bF = int64_t(F) * pack_floats(2 * int64_t(N), Kp);
-    const size_t need = size_t(aF + bF) * sizeof(float) + 256;
-    if (!tc.ws || need > tc.ws_bytes) return false;
-    float* Ap = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tc.ws) + 255) & ~uintptr_t(255));
-    float* Bp = Ap + aF;   // aF is a multiple of 64 floats: Bp stays 256-byte aligned
-
-    CUtensorMap mA, mB, mC;
-    if (!encode3(&mA, Ap, Kp, M, 2 * uint64_t(F), Kp * 4, uint64_t(M) * Kp * 4, kTKf, kTM,
-                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
-        !encode3(&mB, Bp, Kp, 2 * uint64_t(N), 2 * uint64_t(F), Kp * 4, 2 * uint64_t(N) * Kp * 4, kTKf, kTN,
-                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
-        !encode3(&mC, G, 2 * uint64_t(c1), uint64_t(r1), uint64_t(F), uint64_t(ld) * 8, uint64_t(sG) * 8, 32, 32,
-                 CU_TENSOR_MAP_L2_PROMOTION_NONE))
-        return false;
-
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemBytes));
-        attr_set = true;
-    }
-    {
-        ProfScope ps(PK_PACK, 0.0, st);
-        pack_a_kernel<<<dim3(cdiv(int64_t(M) * Kp / 4, 256), F), 256, 0, st>>>(
-            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 2 * k0, 2 * K, int(Kp), Ap);
-        pack_b_kernel<<<dim3(cdiv(Kp / 2, 32), cdiv(N, 32), F), dim3(32, 8), 0, st>>>(G, sG, ld, k0, K, c0, N, int(Kp),
-                                                                                        Bp);
-    }
-    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTKf), g_spin_limit.load(), tc.err};
-    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
-    ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
-    tc_gemm_kernel<<<grid, kThreads, kSmemBytes, st>>>(mA, mB, mC, args);
-    return true;
+    return tc.planes == 1 ? launch_np<1>(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc, st)
+                          : launch_np<3>(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc, st);
 }
 
 }  // namespace fsi

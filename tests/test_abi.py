@@ -195,7 +195,7 @@ def test_invalid_arguments_are_rejected_before_device_work(lib):
     nsing = C.c_int(0)
     assert lib.fsi_batched_lu(1, 1, 4, 4, 5, p, 4, 16, ipiv.ctypes.data_as(C.c_void_p), p, 1024, C.byref(nsing),
                               None) == -1 and "shape" in last()
-    # a precision outside {FP64, FP32_IR, TF32X3_IR} would make the kernels misread the matrices
+    # a precision outside {FP64, FP32_IR, BF16X6_IR, BF16_IR} would make the kernels misread the matrices
     assert lib.fsi_batched_lu(7, 1, 4, 4, 4, p, 4, 16, ipiv.ctypes.data_as(C.c_void_p), p, 1024, C.byref(nsing),
                               None) == -1 and "precision" in last()
     assert lib.fsi_batched_lu_noalloc(7, 1, 4, 4, 4, p, 4, 16, ipiv.ctypes.data_as(C.c_void_p), C.byref(nsing),
@@ -203,7 +203,7 @@ def test_invalid_arguments_are_rejected_before_device_work(lib):
     assert lib.fsi_batched_lu_noalloc(2, 1, 4, 4, 4, p, 4, 16, ipiv.ctypes.data_as(C.c_void_p), C.byref(nsing),
                                       None) == -1 and "workspace" in last()
     need = C.c_size_t(0)
-    assert lib.fsi_lu_workspace(3, 1, 4, 4, 4, C.byref(need)) == -1 and "precision" in last()
+    assert lib.fsi_lu_workspace(7, 1, 4, 4, 4, C.byref(need)) == -1 and "precision" in last()
     assert lib.fsi_set_wait_limit(-1) == -1
     assert lib.rom_residual_check(C.byref(dims), p, p, 4, p, p, p, p, p, 9, dp, 1, 1, p, 1 << 20, dp, None) == -1
     assert lib.rom_sweep(4, p, p, p, p, p, 1, 1, dp, 0, 1, 0, p, 1 << 20, p, None, None, None) == -1

@@ -18,11 +18,12 @@ def _apply_ipiv(A, ipiv):
 
 
 @pytest.mark.parametrize("dtype,tol,tc", [("complex128", 1e-12, False), ("complex64", 2e-5, False),
-                                           ("complex64", 5e-5, True)])
+                                           ("complex64", 2e-5, "bf16x6"), ("complex64", 2e-2, "bf16")])
 @pytest.mark.parametrize("batch,m,ncols,npiv", [(3, 70, 70, 70), (2, 200, 300, 100), (4, 333, 401, 131),
                                                 (1, 1, 1, 1), (2, 130, 130, 65), (2, 300, 650, 200)])
 def test_batched_partial_lu(dtype, tol, tc, batch, m, ncols, npiv):
-    """tc: the trailing updates run on the tcgen05 tensor cores in 3xTF32 (FP32 accuracy)."""
+    """tc: the long trailing updates run on the tcgen05 tensor cores, with three BF16 planes per
+    operand (FP32 accuracy) or one (plain BF16 products, FP32 accumulation)."""
     torch = need_cuda()
     from paper_2310_04734_gb300 import api
     rng = np.random.default_rng(m * 7 + ncols)
@@ -78,7 +79,7 @@ def test_tensor_core_updates_on_a_slab_window():
     rng = np.random.default_rng(852)
     A = rng.standard_normal((2, 2 * b, 3 * b)) + 1j * rng.standard_normal((2, 2 * b, 3 * b))
     errs = {}
-    for tc in (False, True):
+    for tc in (False, "bf16x6"):
         At = torch.tensor(A.astype(np.complex64), device="cuda")
         ipiv, nsing = api.fsi_batched_lu(At, b, tensor_cores=tc)
         torch.cuda.synchronize()
@@ -86,9 +87,9 @@ def test_tensor_core_updates_on_a_slab_window():
         R = At.cpu().numpy().astype(np.complex128)
         piv = ipiv.cpu().numpy()
         errs[tc] = max(_lu_residual(A[i], R[i], piv[i], b) for i in range(2))
-    print("slab window |PA-LU|/|A|: simt %.2e  tcgen05 %.2e" % (errs[False], errs[True]))
+    print("slab window |PA-LU|/|A|: simt %.2e  tcgen05 bf16x6 %.2e" % (errs[False], errs["bf16x6"]))
     assert errs[False] <= 2e-5 * np.sqrt(2 * b)
-    assert errs[True] <= 2.0 * errs[False] + 1e-6
+    assert errs["bf16x6"] <= 1.5 * errs[False]
 
 
 def test_tensor_core_wait_timeout_is_reported_and_the_next_call_is_clean():

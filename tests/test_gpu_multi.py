@@ -1,10 +1,12 @@
 """Persistent multi-model reduced sweep (uneven reduced orders in one launch) against
-the per-model FP64 reduced sweep, and its replay from a captured CUDA graph."""
+the oracle's reduced sweep (dense GEPP, Eq. 11) on the same reduced matrices and
+against the per-model FP64 reduced sweep, and its replay from a captured CUDA graph."""
 import numpy as np
 import pytest
 
 import workloads as W
 from gpu_util import need_cuda, rel
+from oracle import rom as orom
 
 pytestmark = pytest.mark.gpu
 
@@ -45,9 +47,14 @@ def test_multi_sweep_matches_per_model_sweeps():
         pref, splref = api.rom_sweep(rm, f, batch=16)
         pg, pr = p.cpu().numpy(), pref.cpu().numpy()
         KR, DR, MR = (x.cpu().numpy() for x in (rm.KR, rm.DR, rm.MR))
+        # the oracle's reduced sweep on the very same reduced matrices
+        yo = orom.reduced_sweep(orom.ReducedModel(KR=KR, DR=DR, MR=MR, fR=rm.fR.cpu().numpy(),
+                                                  CR=rm.CR.cpu().numpy()), f)
         for i, fi in enumerate(f):
             w = 2 * np.pi * fi
             A = KR + 1j * w * DR - w * w * MR
+            kraw = np.linalg.cond(A, 1)   # the oracle solves the unscaled system
+            assert rel(pg[i], yo[i]) <= max(1e-6, 10 * kraw * u), (rm.k, fi, rel(pg[i], yo[i]), kraw)
             A = A / np.abs(A).max(axis=1, keepdims=True)            # the row equilibration both solvers use
             kappa = np.linalg.cond(A / np.abs(A).max(axis=0, keepdims=True), 1)
             if flagged[m_i][i]:   # only systems an FP32 factor cannot refine are flagged

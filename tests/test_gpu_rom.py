@@ -233,10 +233,15 @@ def test_check_and_resolve_replaces_failing_frequencies_by_full_order():
     freqs = np.array([45.0, 97.0, 150.0, 212.0, 280.0])
     p, spl = api.rom_sweep(rm, freqs, batch=5)
     keep_p, keep_spl = p.clone(), spl.clone()
-    rel_l, res_l, n_l = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=1.0)
-    assert n_l == 0 and not res_l.any() and torch.equal(p, keep_p) and torch.equal(spl, keep_spl)
     ref = api.rom_residual_check(model, V, rm, F, freqs)
+    loose = 2.0 * ref.max()                   # above every residual: nothing fails the check
+    rel_l, res_l, n_l = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=loose)
+    assert n_l == 0 and not res_l.any() and torch.equal(p, keep_p) and torch.equal(spl, keep_spl)
     assert np.allclose(rel_l, ref, rtol=1e-12, atol=0)
+    # a tolerance between the residuals re-solves exactly the frequencies above it
+    mid = float(np.median(ref.max(axis=1)))
+    _, res_m, n_m = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p.clone(), spl.clone(), res_tol=mid)
+    assert n_m == int((ref.max(axis=1) > mid).sum()) and (res_m == (ref.max(axis=1) > mid)).all()
     rel_0, res_0, n_0 = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=0.0)
     assert n_0 == len(freqs) and res_0.all()
     full = api.frf_sweep_full(model, freqs, F, rcv, precision="fp32_ir", batch=5, max_refine=60, tol=1e-10)
