@@ -232,8 +232,12 @@ def run_rom(args):
     grid = w.freqs_hz[(w.freqs_hz >= max(lo, 1.0)) & (w.freqs_hz <= hi)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    wr = api.rom_windows(model, F, rcv, grid, q=args.rom_q, kmax=args.rom_kmax, max_shifts=12, tol=args.rom_tol,
-                         max_windows=args.rom_windows, min_points=8, reuse=not args.rom_no_reuse)
+    P = args.rom_batch_shifts
+    wr = api.rom_windows(model, F, rcv, grid, q=args.rom_q, kmax=args.rom_kmax,
+                         max_shifts=args.rom_max_shifts or (P if P > 1 else 12), tol=args.rom_tol,
+                         max_windows=args.rom_windows, min_points=8, reuse=not args.rom_no_reuse,
+                         precision=args.rom_precision, batch_shifts=P, init_points=args.rom_init_points,
+                         init_windows=args.rom_init_windows)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
@@ -253,7 +257,7 @@ def run_rom(args):
     torch.cuda.empty_cache()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    full = api.frf_sweep_full(model, chk, F, rcv, precision="fp32_ir", batch=min(8, len(chk)), max_refine=60,
+    full = api.frf_sweep_full(model, chk, F, rcv, precision="bf16x6_ir", batch=min(16, len(chk)), max_refine=80,
                               tol=1e-10, allow_noconv=True)
     torch.cuda.synchronize()
     t_full = time.perf_counter() - t0
@@ -272,12 +276,15 @@ def run_rom(args):
         "build_s": t_build, "sweep_ms": t_sweep * 1e3,
         "e2e": {"value": len(grid) / (t_build + t_sweep), "unit": UNIT, "note": "window build + one sweep"},
         "full_order_check": {"value": len(chk) / t_full, "unit": UNIT,
-                             "note": "the check frequencies at full order (FP32 factor + FP64 GMRES to 1e-10)",
+                             "note": "the check frequencies at full order (BF16x6 tensor-core LU + FP64 GMRES "
+                                     "to 1e-10)",
                              "reduced_sweep_speedup": (len(grid) / t_sweep) / (len(chk) / t_full)},
         "check": {"frequencies": int(len(chk)), "max_spl_err_db": float(db.max()),
                   "median_spl_err_db": float(np.median(db)), "max_rel_err": float(relerr.max()),
                   "fom_unconverged": int(full.stats.n_unconverged)},
-        "dtype": "f64 reduced LU; f32 factor + f64 refinement for the moments"}))
+        "build": {"precision": args.rom_precision, "batch_shifts": P, "init_points": args.rom_init_points,
+                  "init_windows": args.rom_init_windows, "q": args.rom_q, "kmax": args.rom_kmax, "tol": args.rom_tol},
+        "dtype": "f64 reduced LU; moments by the %s factor + f64 refinement" % args.rom_precision}))
     return 0
 
 
@@ -455,6 +462,13 @@ def main():
     ap.add_argument("--rom-kmax", type=int, default=400)
     ap.add_argument("--rom-tol", type=float, default=1e-4)
     ap.add_argument("--rom-windows", type=int, default=16)
+    ap.add_argument("--rom-batch-shifts", type=int, default=1,
+                    help="expansion points factored and solved together; with > 1 every window is built from "
+                         "that many points at once (no greedy additions, failing windows are bisected)")
+    ap.add_argument("--rom-init-points", type=int, default=0)
+    ap.add_argument("--rom-init-windows", type=int, default=1)
+    ap.add_argument("--rom-max-shifts", type=int, default=0)
+    ap.add_argument("--rom-precision", default="fp32_ir", choices=["fp32_ir", "bf16x6_ir", "fp64"])
     ap.add_argument("--rom-no-reuse", action="store_true",
                     help="windows start from fresh points instead of their enclosing windows' points")
     ap.add_argument("--design-shifts", type=int, default=16)
@@ -507,7 +521,7 @@ def main():
                    api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers), host_io=True))
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    kw = dict(precision=args.precision, batch=B, max_refine=60, tol=REFINE_TOL, workspace=ws, allow_noconv=True)
+    kw = dict(precision=args.precision, batch=B, max_refine=160, tol=REFINE_TOL, workspace=ws, allow_noconv=True)
     for s in range(args.warmup):
         api.frf_sweep_full(model, batch_freqs(s), F, rcv, **kw)
     torch.cuda.synchronize()

@@ -247,10 +247,14 @@ fsi_status fsi_batched_lu_noalloc(int precision, int batch, int m, int ncols, in
                                   void* stream);
 
 typedef struct {
-    int precision;                /* factorisation per expansion point             */
-    int max_refine;               /* refinement cap per moment solve (FP32_IR)     */
+    int precision;                /* factorisation per expansion point: FSI_FP64,  */
+                                  /* FSI_FP32_IR or FSI_BF16X6_IR                   */
+    int max_refine;               /* refinement cap per moment solve               */
     double tol;                   /* refinement tolerance per moment solve         */
     int second_order;             /* -1 auto (Eq. 9 if D != 0, else Eq. 10), 0, 1 */
+    int batch_shifts;             /* expansion points factored, and their Eq. 10   */
+                                  /* moments solved, together (0 or 1: one at a    */
+                                  /* time; at most 64; Eq. 9 runs one at a time)   */
 } fsi_rom_opts;
 
 /* Workspace bytes for rom_build. */
@@ -464,6 +468,13 @@ typedef struct {
                                      their Krylov blocks copied from a moment store
                                      (no new factorisation); 0: fresh points at the
                                      window's quarter midpoints                      */
+    int init_points;              /* initial expansion points of a fresh window: the
+                                     candidates nearest the midpoints of this many equal
+                                     parts of it (0: 4, the quarter midpoints); with
+                                     greedy.build.batch_shifts >= init_points they are
+                                     factored and solved together                     */
+    int init_windows;             /* the band starts as this many windows of equal
+                                     candidate counts (0 or 1: one window)            */
 } fsi_window_opts;
 
 /* Workspace bytes for rom_windows (one greedy workspace + an n x kmax basis, and with

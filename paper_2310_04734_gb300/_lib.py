@@ -52,7 +52,7 @@ MLP_PARAMS = 4609
 
 class fsi_rom_opts(C.Structure):
     _fields_ = [("precision", c_int), ("max_refine", c_int), ("tol", C.c_double),
-                ("second_order", c_int)]
+                ("second_order", c_int), ("batch_shifts", c_int)]
 
 
 class fsi_greedy_opts(C.Structure):
@@ -61,7 +61,8 @@ class fsi_greedy_opts(C.Structure):
 
 
 class fsi_window_opts(C.Structure):
-    _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int), ("reuse", c_int)]
+    _fields_ = [("greedy", fsi_greedy_opts), ("max_windows", c_int), ("min_points", c_int), ("reuse", c_int),
+                ("init_points", c_int), ("init_windows", c_int)]
 
 
 class fsi_rom_item(C.Structure):

@@ -261,23 +261,25 @@ def fsi_batched_lu_noalloc(A, npiv: int):
     return ipiv, nsing.value
 
 
-def _rom_opts(precision="fp32_ir", max_refine=10, tol=1e-10, second_order=-1):
+def _rom_opts(precision="fp32_ir", max_refine=10, tol=1e-10, second_order=-1, batch_shifts=1):
     o = L.fsi_rom_opts()
     o.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
     o.max_refine = int(max_refine)
     o.tol = float(tol)
     o.second_order = int(second_order)
+    o.batch_shifts = int(batch_shifts)
     return o
 
 
 def rom_build(model: DeviceModel, shifts_hz, q: int, F, kmax: int, precision="fp32_ir", max_refine=10,
-              tol=1e-10, second_order=-1):
-    """Rational Arnoldi basis V (n x k complex128, column-major as a [k][n] tensor transposed)."""
+              tol=1e-10, second_order=-1, batch_shifts=1):
+    """Rational Arnoldi basis V (n x k complex128, column-major as a [k][n] tensor transposed);
+    batch_shifts expansion points are factored and their first-order moments solved together."""
     torch = _torch()
     lib = L.load()
     s = np.ascontiguousarray(np.asarray(shifts_hz, dtype=np.float64))
     nrhs = F.shape[1]
-    o = _rom_opts(precision, max_refine, tol, second_order)
+    o = _rom_opts(precision, max_refine, tol, second_order, batch_shifts)
     need = C.c_size_t()
     L.check(lib.rom_workspace(C.byref(model.dims), nrhs, q, kmax, C.byref(o), C.byref(need)), "rom_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")
@@ -483,7 +485,7 @@ class GreedyResult:
 
 def rom_greedy(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
                init_hz=None, precision="fp32_ir", max_refine=10, refine_tol=1e-10,
-               second_order=-1, mlp_params=None) -> GreedyResult:
+               second_order=-1, mlp_params=None, batch_shifts=1) -> GreedyResult:
     """Greedy expansion points with the Gram-block residual estimate (C-ABI rom_greedy)."""
     torch = _torch()
     lib = L.load()
@@ -493,7 +495,7 @@ def rom_greedy(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shift
     nrhs = F.shape[1]
     o = L.fsi_greedy_opts()
     o.q, o.kmax, o.max_shifts, o.tol = int(q), int(kmax), int(max_shifts), float(tol)
-    o.build = _rom_opts(precision, max_refine, refine_tol, second_order)
+    o.build = _rom_opts(precision, max_refine, refine_tol, second_order, batch_shifts)
     o.mlp = _ptr(mlp_params) if mlp_params is not None else None
     need = C.c_size_t()
     L.check(lib.rom_greedy_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_greedy_workspace")
@@ -543,7 +545,8 @@ class WindowedROM:
 
 def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shifts: int, tol: float,
                 max_windows: int = 16, min_points: int = 4, precision="fp32_ir", max_refine=10,
-                refine_tol=1e-10, second_order=-1, reuse: bool = True) -> WindowedROM:
+                refine_tol=1e-10, second_order=-1, reuse: bool = True, batch_shifts=1, init_points=0,
+                init_windows=1) -> WindowedROM:
     """Local ROMs over windows of the candidate band (C-ABI rom_windows); with reuse, a window
     split from a larger one starts from that window's expansion points in its band."""
     torch = _torch()
@@ -552,8 +555,9 @@ def rom_windows(model: DeviceModel, F, rcv, cand_hz, q: int, kmax: int, max_shif
     nrhs = F.shape[1]
     o = L.fsi_window_opts()
     o.greedy.q, o.greedy.kmax, o.greedy.max_shifts, o.greedy.tol = int(q), int(kmax), int(max_shifts), float(tol)
-    o.greedy.build = _rom_opts(precision, max_refine, refine_tol, second_order)
+    o.greedy.build = _rom_opts(precision, max_refine, refine_tol, second_order, batch_shifts)
     o.max_windows, o.min_points, o.reuse = int(max_windows), int(min_points), int(bool(reuse))
+    o.init_points, o.init_windows = int(init_points), int(init_windows)
     need = C.c_size_t()
     L.check(lib.rom_windows_workspace(C.byref(model.dims), nrhs, C.byref(o), C.byref(need)), "rom_windows_workspace")
     ws = torch.empty(need.value, dtype=torch.uint8, device="cuda")

@@ -185,10 +185,10 @@ template <typename R>
 fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev, int nrhs,
                     double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
                     double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done,
-                    std::vector<double>& rel, cudaStream_t st) {
+                    std::vector<double>& rel, cudaStream_t st, int64_t sB) {
     std::vector<double> hn(size_t(Fb) * nrhs), hf(size_t(Fb) * nrhs), ha(size_t(Fb) * nrhs);
     FSI_CUDA(cudaMemsetAsync(fnorms, 0, sizeof(double) * Fb * nrhs, st));
-    launch_residual(m, d_omega, 0.0, Fb, nullptr, sV, Bdev, nrhs, rhat, sV, fnorms, true, st);
+    launch_residual(m, d_omega, 0.0, Fb, nullptr, sV, Bdev, nrhs, rhat, sV, fnorms, true, st, nullptr, sB);
     FSI_CHECK_LAUNCH();
     FSI_CUDA(cudaMemcpyAsync(norms, fnorms, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToDevice, st));
     FSI_CUDA(cudaMemcpyAsync(hf.data(), fnorms, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
@@ -202,7 +202,7 @@ fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_om
         launch_update<R>(xhat, sV, norms, y, sV, m.n, nrhs, Fb, nullptr, st);
         FSI_CUDA(cudaMemsetAsync(norms, 0, sizeof(double) * Fb * nrhs, st));
         FSI_CUDA(cudaMemsetAsync(absn, 0, sizeof(double) * Fb * nrhs, st));
-        launch_residual(m, d_omega, 0.0, Fb, xhat, sV, Bdev, nrhs, rhat, sV, norms, true, st, absn);
+        launch_residual(m, d_omega, 0.0, Fb, xhat, sV, Bdev, nrhs, rhat, sV, norms, true, st, absn, sB);
         FSI_CHECK_LAUNCH();
         FSI_CUDA(cudaMemcpyAsync(hn.data(), norms, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
         FSI_CUDA(cudaMemcpyAsync(ha.data(), absn, sizeof(double) * Fb * nrhs, cudaMemcpyDeviceToHost, st));
@@ -337,10 +337,10 @@ template fsi_status factor_batch<float>(const DevModel&, Factor<float>&, int, co
 template fsi_status factor_batch<double>(const DevModel&, Factor<double>&, int, const double*, cudaStream_t);
 template fsi_status ir_solve<float>(const DevModel&, Factor<float>&, int, const double*, const double2*, int,
                                     double2*, double2*, float2*, double*, double*, double*, int64_t, int, double,
-                                    std::vector<int>&, std::vector<double>&, cudaStream_t);
+                                    std::vector<int>&, std::vector<double>&, cudaStream_t, int64_t);
 template fsi_status ir_solve<double>(const DevModel&, Factor<double>&, int, const double*, const double2*, int,
                                      double2*, double2*, double2*, double*, double*, double*, int64_t, int, double,
-                                     std::vector<int>&, std::vector<double>&, cudaStream_t);
+                                     std::vector<int>&, std::vector<double>&, cudaStream_t, int64_t);
 
 }  // namespace fsi
 
@@ -504,6 +504,7 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
         if (tensor) {
             const size_t off = align_up(sizeof(int32_t) * size_t(batch + 1));
             tc.planes = tc_planes(precision);
+            tc.a_bytes = tc_a_region_bytes(batch, m, ncols, npiv, tc.planes);
             tc.err = status + batch;
             tc.ws = static_cast<char*>(ws) + off;
             tc.ws_bytes = ws_bytes - off;

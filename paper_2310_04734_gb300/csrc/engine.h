@@ -43,6 +43,7 @@ struct Factor {
         if (planes > 0 && sizeof(R) == 4) {
             tc.planes = planes;
             tc.ws_bytes = tc_workspace_bytes(F, 2 * d.b, 3 * d.b, d.b, planes);
+            tc.a_bytes = tc_a_region_bytes(F, 2 * d.b, 3 * d.b, d.b, planes);
             tc.ws = c.take<char>(tc.ws_bytes);
         }
     }
@@ -62,11 +63,13 @@ fsi_status factor_batch(const DevModel& m, Factor<R>& fc, int F, const double* d
 // residual, correction by the stored factors in precision R.  On return xhat
 // holds the scaled solution (x = cs o xhat); it_done[f] is the first iteration
 // whose relative residual reached tol or the rounding floor (-1: neither), rel[f]
-// the last relative residual.  absn: F*nrhs scratch for the floor.
+// the last relative residual.  absn: F*nrhs scratch for the floor.  sB: stride between the
+// frequencies' right-hand sides in Bdev (0: one right-hand side block for all of them).
 template <typename R>
 fsi_status ir_solve(const DevModel& m, Factor<R>& fc, int Fb, const double* d_omega, const double2* Bdev, int nrhs,
                     double2* xhat, double2* rhat, typename Cplx<R>::T* y, double* norms, double* fnorms,
-                    double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st);
+                    double* absn, int64_t sV, int max_it, double tol, std::vector<int>& it_done, std::vector<double>& rel, cudaStream_t st,
+                    int64_t sB = 0);
 
 // Forward and backward slab solves of y (F frequencies, nrhs columns each, stride sY);
 // with flist (device, nF entries) only the listed frequencies are solved.

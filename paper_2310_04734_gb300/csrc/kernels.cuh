@@ -136,9 +136,24 @@ struct TcCtx {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int planes = 3;   // BF16 planes per operand: 3 (six products, FP32 level) or 1 (plain BF16)
+    size_t a_bytes = 0;   // the first a_bytes of ws hold the A operand of one update
+    // the U12 columns [bc0, bc0 + bN) of the current slab step, packed block by block after ws + a_bytes
+    void* bpack = nullptr;
+    int64_t bKp = 0;
+    int bN = 0, bc0 = 0;
 };
-// Workspace bytes for every trailing update of partial_lu(F, m, ncols, npiv) on the tensor cores.
+// Workspace bytes for every trailing update of partial_lu(F, m, ncols, npiv) on the tensor cores,
+// and the part of it that holds the A operand of one update.
 size_t tc_workspace_bytes(int F, int m, int ncols, int npiv, int planes);
+size_t tc_a_region_bytes(int F, int m, int ncols, int npiv, int planes);
+// Columns [c0, c1) right of the npiv pivots: prepare the packed U12 operand (false: the tensor-core
+// path does not apply; use launch_tc_update / the SIMT update).  Then tc_pack_b_rows packs rows
+// [k_begin, k_end) of U12 once they are final, and launch_tc_update_lazy runs
+// C[r0:r1, c0:c1] -= A[r0:r1, 0:K] U12[0:K, c0:c1] from the packed rows.
+bool tc_begin_lazy(float2* G, int64_t sG, int ld, int F, int npiv, int c0, int c1, TcCtx& tc, cudaStream_t st);
+void tc_pack_b_rows(float2* G, int64_t sG, int ld, int F, int k_begin, int k_end, const TcCtx& tc, cudaStream_t st);
+bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc,
+                           cudaStream_t st);
 // Spin limit of the tensor-core kernels' pipeline waits (0: the default, about 6.7e7 polls).
 void set_tc_spin_limit(uint32_t spins);
 // Trailing update C -= A B of the FP32 band LU on tcgen05 tensor cores (BF16 planes, TMA-fed).
@@ -185,10 +200,11 @@ void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, in
 // x may be NULL (x = 0).  Accumulates |r|^2 per (f, column) into norms if non-NULL.
 // omega per batch member from d_omega, or the scalar omega0 when d_omega is NULL.
 // absn (optional) accumulates |rs o (|A| |cs o x| + |F|)|^2 per (f, column): the size of the
-// terms whose FP64 rounding bounds the attainable residual.
+// terms whose FP64 rounding bounds the attainable residual.  sF: stride between the
+// frequencies' right-hand sides (0: Fm is shared by all of them).
 void launch_residual(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x,
                      int64_t sX, const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms,
-                     bool scaled, cudaStream_t st, double* absn = nullptr);
+                     bool scaled, cudaStream_t st, double* absn = nullptr, int64_t sF = 0);
 // y = (T)(r / s) with s = sqrt(norms) per (f, column)
 template <typename R>
 void launch_to_low(const double2* r, int64_t sR, const double* norms, typename Cplx<R>::T* y, int64_t sY,

@@ -563,12 +563,31 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
         }
     }
     if (npiv < ncols) {
+        // on the tensor cores the rows of U12 are packed once, block by block as they are solved
+        TcCtx lz;
+        bool lazy = false;
+        if constexpr (sizeof(R) == 4) {
+            if (tc) {
+                lz = *tc;
+                lazy = tc_begin_lazy(G, sG, ld, F, npiv, npiv, ncols, lz, st);
+            }
+        }
+        auto update = [&](int r0, int r1, int K) {
+            if constexpr (sizeof(R) == 4) {
+                if (lazy && launch_tc_update_lazy(G, sG, ld, F, r0, r1, K, lz, st)) return;
+                lazy = false;   // the packed rows are not kept up to date from here on
+            }
+            trailing_update<R>(G, sG, ld, F, r0, r1, npiv, ncols, 0, K, tc, st);
+        };
         for (int I = 0; I < npiv; I += kLazyTrsmRows) {
             const int tb = std::min(kLazyTrsmRows, npiv - I);
-            if (I > 0) trailing_update<R>(G, sG, ld, F, I, I + tb, npiv, ncols, 0, I, tc, st);
+            if (I > 0) update(I, I + tb, I);
             blocked_trsm<R>(G, sG, ld, F, I, tb, npiv, ncols, st);
+            if constexpr (sizeof(R) == 4) {
+                if (lazy) tc_pack_b_rows(G, sG, ld, F, I, I + tb, lz, st);
+            }
         }
-        if (npiv < m) trailing_update<R>(G, sG, ld, F, npiv, m, npiv, ncols, 0, npiv, tc, st);
+        if (npiv < m) update(npiv, m, npiv);
     }
 }
 

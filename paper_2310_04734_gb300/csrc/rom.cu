@@ -472,48 +472,67 @@ fsi_status cgs2_append(double2* V, int64_t n, int& k, int kmax, double2* w, CgsB
     return FSI_OK;
 }
 
+// expansion points factored and solved together, and BF16 planes of the tensor-core updates
+int rom_points(const fsi_rom_opts& o) { return std::max(1, std::min(o.batch_shifts, 64)); }
+int rom_planes(const fsi_rom_opts& o) { return o.precision == FSI_BF16X6_IR ? 3 : 0; }
+
 template <typename R>
 struct RomWS {
     using T2 = typename Cplx<R>::T;
     Factor<R> fc;
-    double* omega;
-    double2 *xhat, *rhat, *X, *B, *W;
-    T2* y;
-    double *norms, *fnorms, *absn;
+    double* omega;                       // P
+    double2 *xhat, *rhat, *X, *B, *W;    // P x sV each (W: n)
+    T2* y;                               // P x sV
+    double *norms, *fnorms, *absn;       // P x nrhs
     CgsBufs cg;
     double2 *Qs, *Ps;
-    double2* Ql;   // local Krylov block of one expansion point (first order), n x q*nrhs
+    double2* Ql;   // local Krylov blocks of P expansion points (first order), P x n x q*nrhs
     int64_t sV;
+    int P;
 
-    void carve(Carver& c, const fsi_dims& d, int nrhs, int q, int kmax) {
-        fc.carve(c, d, 1, nrhs);
+    void carve(Carver& c, const fsi_dims& d, int nrhs, int q, int kmax, int points, int planes) {
+        P = points;
+        fc.carve(c, d, P, nrhs, planes);
+        fc.use_tc = planes > 0;
         sV = int64_t(nrhs) * d.n;
-        omega = c.take<double>(1);
-        xhat = c.take<double2>(sV);
-        rhat = c.take<double2>(sV);
-        X = c.take<double2>(sV);
-        B = c.take<double2>(sV);
+        omega = c.take<double>(P);
+        xhat = c.take<double2>(P * sV);
+        rhat = c.take<double2>(P * sV);
+        X = c.take<double2>(P * sV);
+        B = c.take<double2>(P * sV);
         W = c.take<double2>(d.n);
-        y = c.take<T2>(sV);
-        norms = c.take<double>(nrhs);
-        fnorms = c.take<double>(nrhs);
-        absn = c.take<double>(nrhs);
+        y = c.take<T2>(P * sV);
+        norms = c.take<double>(size_t(P) * nrhs);
+        fnorms = c.take<double>(size_t(P) * nrhs);
+        absn = c.take<double>(size_t(P) * nrhs);
         const int kk = std::max(kmax, q) + 1;
         cg.partial = c.take<double2>(size_t(kChunks) * kk * std::max(nrhs, 1));
         cg.H = c.take<double2>(size_t(kk) * std::max(nrhs, 1));
         cg.scal = c.take<double>(2);
         Qs = c.take<double2>(size_t(d.n) * q);
         Ps = c.take<double2>(size_t(d.n) * q);
-        Ql = c.take<double2>(size_t(d.n) * q * nrhs);
+        Ql = c.take<double2>(size_t(P) * d.n * q * nrhs);
     }
 };
 
 template <typename R>
-size_t rom_ws_bytes(const fsi_dims& d, int nrhs, int q, int kmax) {
+size_t rom_ws_bytes(const fsi_dims& d, int nrhs, int q, int kmax, const fsi_rom_opts& o) {
     Carver c(nullptr, 0);
     RomWS<R> w;
-    w.carve(c, d, nrhs, q, kmax);
+    w.carve(c, d, nrhs, q, kmax, rom_points(o), rom_planes(o));
     return align_up(c.used);
+}
+
+// x_f = sign * (cs(w_f) o xhat_f) for the F points of a batch
+__global__ void unscale_batch_kernel(DevModel m, const double* omega, const double2* xhat, double2* x, int nrhs,
+                                     int64_t sV, double sign) {
+    const int f = blockIdx.y;
+    const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (q >= m.n * nrhs) return;
+    const int64_t i = q % m.n;
+    const double s = sign * col_scale(m, i, omega[f]);
+    const double2 v = xhat[f * sV + q];
+    x[f * sV + q] = make_double2(s * v.x, s * v.y);
 }
 
 // X = x(w_j) for right-hand sides B (n x nr): refined solve, unscaled, times `sign`.
@@ -536,7 +555,7 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
                          double2* V, int k_in, int* k_out, cudaStream_t st, MomentStore* store) {
     Carver c(ws, ws_bytes);
     RomWS<R> w;
-    w.carve(c, d, nrhs, q, kmax);
+    w.carve(c, d, nrhs, q, kmax, rom_points(o), rom_planes(o));
     if (!c.fits()) {
         set_error("rom workspace too small");
         return FSI_ENOMEM;
@@ -562,57 +581,99 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
         second = o.second_order != 0;
     }
     int k = k_in;   // columns already in V (orthonormal)
-    std::vector<int32_t> hstat(1);
-    for (int sidx = 0; sidx < nshift && k < kmax; ++sidx) {
-        const double om = 2.0 * M_PI * shifts[sidx];
-        ROM_CUDA(cudaMemcpyAsync(w.omega, &om, sizeof(double), cudaMemcpyHostToDevice, st));
-        fsi_status s = factor_batch<R>(m, w.fc, 1, w.omega, st);
+    const int P = second ? 1 : w.P;   // SOAR runs one point at a time
+    std::vector<int32_t> hstat(P);
+    for (int g0 = 0; g0 < nshift && k < kmax;) {
+        const int Pg = std::min(P, nshift - g0);
+        std::vector<double> omv(Pg);
+        for (int p = 0; p < Pg; ++p) omv[p] = 2.0 * M_PI * shifts[g0 + p];
+        const double om = omv[0];
+        const int sidx = g0;
+        ROM_CUDA(cudaMemcpyAsync(w.omega, omv.data(), sizeof(double) * Pg, cudaMemcpyHostToDevice, st));
+        fsi_status s = factor_batch<R>(m, w.fc, Pg, w.omega, st);
         if (s != FSI_OK) return s;
-        ROM_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        ROM_CUDA(cudaMemcpyAsync(hstat.data(), w.fc.status, sizeof(int32_t) * Pg, cudaMemcpyDeviceToHost, st));
         ROM_CUDA(cudaStreamSynchronize(st));
-        if (hstat[0]) {
-            set_error("singular shifted matrix at an expansion point");
-            return FSI_ESINGULAR;
+        for (int p = 0; p < Pg; ++p)
+            if (hstat[p]) {
+                set_error("singular shifted matrix at an expansion point");
+                return FSI_ESINGULAR;
+            }
+        g0 += Pg;
+        if (!second) {
+            // Eq. 10 at Pg points at once: per point a local Arnoldi on Kt^-1 M started from
+            // Kt^-1 F (the point's own Krylov space, orthonormalised within the point), the
+            // solves of all points batched; afterwards the accepted local vectors of each point,
+            // in point order, are CGS2-appended to V
+            const int klmax = q * nrhs;
+            std::vector<double2*> Ql(Pg);
+            std::vector<char> keep(Pg, 0);
+            std::vector<int64_t> col0(Pg, 0);
+            int64_t next = store ? store->used : 0;
+            for (int p = 0; p < Pg; ++p) {
+                keep[p] = store && next + klmax <= store->cap;
+                col0[p] = keep[p] ? next : 0;
+                if (keep[p]) next += klmax;
+                Ql[p] = keep[p] ? store->buf + col0[p] * n : w.Ql + int64_t(p) * n * klmax;
+            }
+            std::vector<int> kl(Pg, 0), nr(Pg, nrhs);
+            for (int p = 0; p < Pg; ++p)
+                ROM_CUDA(cudaMemcpyAsync(w.B + p * w.sV, F, sizeof(double2) * n * nrhs, cudaMemcpyDeviceToDevice,
+                                         st));
+            std::vector<int> done;
+            std::vector<double> rel;
+            for (int mom = 0; mom < q; ++mom) {
+                bool any = false;
+                for (int p = 0; p < Pg; ++p) any = any || nr[p] > 0;
+                if (!any) break;
+                s = ir_solve<R>(m, w.fc, Pg, w.omega, w.B, nrhs, w.xhat, w.rhat, w.y, w.norms, w.fnorms, w.absn,
+                                w.sV, max_it, tol, done, rel, st, w.sV);
+                if (s != FSI_OK) return s;
+                unscale_batch_kernel<<<dim3(cdiv(n * nrhs, 256), Pg), 256, 0, st>>>(m, w.omega, w.xhat, w.X, nrhs,
+                                                                                   w.sV, 1.0);
+                ROM_LAUNCH();
+                for (int p = 0; p < Pg; ++p) {
+                    const int kl0 = kl[p];
+                    for (int cc = 0; cc < nr[p]; ++cc) {
+                        bool acc = false;
+                        s = cgs2_append(Ql[p], n, kl[p], klmax, w.X + p * w.sV + int64_t(cc) * n, w.cg, acc, st);
+                        if (s != FSI_OK) return s;
+                    }
+                    nr[p] = kl[p] - kl0;
+                    double2* Bp = w.B + p * w.sV;
+                    if (mom + 1 < q && nr[p] > 0) {
+                        spmv_kernel<<<dim3(spmv_grid_x(n, nr[p]), nr[p]), kRowThreads, 0, st>>>(
+                            m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), Ql[p] + int64_t(kl0) * n,
+                            Bp, nr[p], false);
+                        ROM_LAUNCH();
+                    }
+                    if (nr[p] < nrhs)   // columns without a new direction solve zero right-hand sides
+                        ROM_CUDA(cudaMemsetAsync(Bp + int64_t(nr[p]) * n, 0, sizeof(double2) * n * (nrhs - nr[p]),
+                                                 st));
+                }
+            }
+            for (int p = 0; p < Pg && k < kmax; ++p) {
+                for (int j = 0; j < kl[p] && k < kmax; ++j) {
+                    ROM_CUDA(cudaMemcpyAsync(w.W, Ql[p] + int64_t(j) * n, sizeof(double2) * n,
+                                             cudaMemcpyDeviceToDevice, st));
+                    bool acc = false;
+                    s = cgs2_append(V, n, k, kmax, w.W, w.cg, acc, st);
+                    if (s != FSI_OK) return s;
+                }
+                // a block cut short by the column budget is not the point's whole Krylov space: not kept
+                if (keep[p] && kl[p] > 0 && k < kmax) {
+                    store->blocks.push_back(MomentBlock{shifts[sidx + p], col0[p], kl[p], store->lo, store->hi});
+                    store->used = col0[p] + kl[p];
+                }
+            }
+            continue;
         }
         // room in the store for this point's block (else the local block stays in the workspace)
         const int64_t blk_cols = int64_t(q) * nrhs;
         const bool keep = store && store->used + blk_cols <= store->cap;
         const int64_t col0 = keep ? store->used : 0;
         int nkept = 0;
-        if (!second) {
-            // Eq. 10: local Arnoldi on Kt^-1 M started from Kt^-1 F (the point's own Krylov space,
-            // orthonormalised within the point); each accepted local vector is then CGS2-appended to V
-            double2* Ql = keep ? store->buf + col0 * n : w.Ql;
-            int kl = 0;
-            const int klmax = q * nrhs;
-            ROM_CUDA(cudaMemcpyAsync(w.B, F, sizeof(double2) * n * nrhs, cudaMemcpyDeviceToDevice, st));
-            int nr = nrhs;
-            for (int mom = 0; mom < q && nr > 0 && k < kmax; ++mom) {
-                s = shifted_solve<R>(m, w, om, w.B, nr, max_it, tol, 1.0, w.X, st);
-                if (s != FSI_OK) return s;
-                const int kl0 = kl;
-                for (int cc = 0; cc < nr; ++cc) {
-                    bool acc = false;
-                    s = cgs2_append(Ql, n, kl, klmax, w.X + int64_t(cc) * n, w.cg, acc, st);
-                    if (s != FSI_OK) return s;
-                }
-                for (int j = kl0; j < kl && k < kmax; ++j) {
-                    ROM_CUDA(cudaMemcpyAsync(w.W, Ql + int64_t(j) * n, sizeof(double2) * n, cudaMemcpyDeviceToDevice,
-                                             st));
-                    bool acc = false;
-                    s = cgs2_append(V, n, k, kmax, w.W, w.cg, acc, st);
-                    if (s != FSI_OK) return s;
-                }
-                nr = kl - kl0;
-                if (nr > 0 && mom + 1 < q) {
-                    spmv_kernel<<<dim3(spmv_grid_x(n, nr), nr), kRowThreads, 0, st>>>(
-                        m, make_double2(0, 0), make_double2(0, 0), make_double2(1, 0), Ql + int64_t(kl0) * n, w.B, nr,
-                        false);
-                    ROM_LAUNCH();
-                }
-            }
-            nkept = kl;
-        } else {
+        {
             // Eq. 9 by SOAR per load column: q_0 = u/|u|, u = -Kt^-1 f; r = A q_j + B p_j
             const double2 dt = make_double2(0.0, 2.0 * om);   // Dt = D + 2 i w_j M
             for (int cc = 0; cc < nrhs && k < kmax; ++cc) {
@@ -700,8 +761,8 @@ fsi_status run_rom_build(const fsi_dims& d, const void* d_model, const double* s
 }  // namespace
 
 template <typename R>
-size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax) {
-    return rom_ws_bytes<R>(d, nrhs, q, kmax);
+size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax, const fsi_rom_opts& o) {
+    return rom_ws_bytes<R>(d, nrhs, q, kmax, o);
 }
 
 template <typename R>
@@ -741,8 +802,8 @@ fsi_status rom_append_columns(double2* V, int64_t n, int& k, int kmax, const dou
     return FSI_OK;
 }
 
-template size_t rom_build_ws<float>(const fsi_dims&, int, int, int);
-template size_t rom_build_ws<double>(const fsi_dims&, int, int, int);
+template size_t rom_build_ws<float>(const fsi_dims&, int, int, int, const fsi_rom_opts&);
+template size_t rom_build_ws<double>(const fsi_dims&, int, int, int, const fsi_rom_opts&);
 template fsi_status rom_build_append<float>(const fsi_dims&, const void*, const double*, int, int, const double2*, int,
                                             int, const fsi_rom_opts&, void*, size_t, double2*, int, int*,
                                             cudaStream_t, MomentStore*);
@@ -816,8 +877,10 @@ extern "C" {
 
 fsi_status rom_workspace(const fsi_dims* dims, int nrhs, int q, int kmax, const fsi_rom_opts* opts, size_t* bytes) {
     ROM_REQUIRE(dims && opts && bytes && nrhs > 0 && nrhs <= 8 && q > 0 && kmax > 0, "bad rom workspace arguments");
-    *bytes = opts->precision == FSI_FP64 ? rom_ws_bytes<double>(*dims, nrhs, q, kmax)
-                                         : rom_ws_bytes<float>(*dims, nrhs, q, kmax);
+    ROM_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR || opts->precision == FSI_BF16X6_IR,
+                "unknown precision");
+    *bytes = opts->precision == FSI_FP64 ? rom_ws_bytes<double>(*dims, nrhs, q, kmax, *opts)
+                                         : rom_ws_bytes<float>(*dims, nrhs, q, kmax, *opts);
     return FSI_OK;
 }
 
@@ -826,7 +889,8 @@ fsi_status rom_build(const fsi_dims* dims, const void* d_model, const double* sh
                      fsi_c64* V, int* k_out, void* stream) {
     ROM_REQUIRE(dims && d_model && shifts_hz && F && opts && ws && V && k_out, "NULL argument");
     ROM_REQUIRE(nshift > 0 && q > 0 && nrhs > 0 && nrhs <= 8 && kmax > 0 && kmax <= dims->n, "bad rom sizes");
-    ROM_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR, "unknown precision");
+    ROM_REQUIRE(opts->precision == FSI_FP64 || opts->precision == FSI_FP32_IR || opts->precision == FSI_BF16X6_IR,
+                "unknown precision");
     for (int i = 0; i < nshift; ++i) ROM_REQUIRE(shifts_hz[i] > 0.0, "expansion points must be > 0 Hz");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const double2* Fd = reinterpret_cast<const double2*>(F);

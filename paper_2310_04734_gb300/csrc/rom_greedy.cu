@@ -270,7 +270,7 @@ struct GreedyWS {
     void carve(Carver& c, const fsi_dims& d, int nrhs, const fsi_greedy_opts& o) {
         const int64_t n = d.n;
         const int K = o.kmax;
-        build_bytes = rom_build_ws<R>(d, nrhs, o.q, K);
+        build_bytes = rom_build_ws<R>(d, nrhs, o.q, K, o.build);
         build = c.take<char>(build_bytes);
         ldp = K;
         ldg = 3 * int64_t(K);
@@ -530,7 +530,12 @@ fsi_status run_windows(const fsi_dims& d, const void* d_model, const double2* F,
         int i0, i1;
         std::vector<double> shifts;
     };
-    std::vector<Range> todo{{0, ncand}};
+    // initial partition: init_windows windows of (nearly) equal candidate counts
+    std::vector<Range> todo;
+    {
+        const int nw0 = std::max(1, std::min(o.init_windows, std::max(1, ncand / std::max(1, o.min_points))));
+        for (int i = 0; i < nw0; ++i) todo.push_back(Range{int(int64_t(ncand) * i / nw0), int(int64_t(ncand) * (i + 1) / nw0)});
+    }
     std::vector<Ancestor> anc;   // bisected windows, outermost first
     std::vector<double> shifts(o.greedy.max_shifts), hist(o.greedy.max_shifts), est(ncand);
     out.clear();
@@ -571,9 +576,11 @@ fsi_status run_windows(const fsi_dims& d, const void* d_model, const double2* F,
             }
         }
         if (seed.empty() && init.empty()) {
-            // initial points: the candidates nearest the window's quarter midpoints
-            for (int qq = 0; qq < 4 && int(init.size()) < o.greedy.max_shifts; ++qq) {
-                const double t = c[0] + (c[nc - 1] - c[0]) * (qq + 0.5) / 4.0;
+            // initial points: the candidates nearest the midpoints of init_points equal parts of
+            // the window (4 parts: the quarter midpoints)
+            const int npts = o.init_points > 0 ? o.init_points : 4;
+            for (int qq = 0; qq < npts && int(init.size()) < o.greedy.max_shifts; ++qq) {
+                const double t = c[0] + (c[nc - 1] - c[0]) * (qq + 0.5) / double(npts);
                 int best = 0;
                 for (int i = 1; i < nc; ++i)
                     if (std::fabs(c[i] - t) < std::fabs(c[best] - t)) best = i;
@@ -683,7 +690,7 @@ fsi_status rom_windows(const fsi_dims* dims, const void* d_model, const fsi_c64*
         set_error("rom_windows: bad sizes");
         return FSI_EINVAL;
     }
-    if (!(g.build.precision == FSI_FP64 || g.build.precision == FSI_FP32_IR)) {
+    if (!(g.build.precision == FSI_FP64 || g.build.precision == FSI_FP32_IR || g.build.precision == FSI_BF16X6_IR)) {
         set_error("rom_windows: unknown precision");
         return FSI_EINVAL;
     }
@@ -808,7 +815,7 @@ fsi_status rom_greedy(const fsi_dims* dims, const void* d_model, const fsi_c64* 
         set_error("rom_greedy: bad sizes");
         return FSI_EINVAL;
     }
-    if (!(o->build.precision == FSI_FP64 || o->build.precision == FSI_FP32_IR)) {
+    if (!(o->build.precision == FSI_FP64 || o->build.precision == FSI_FP32_IR || o->build.precision == FSI_BF16X6_IR)) {
         set_error("rom_greedy: unknown precision");
         return FSI_EINVAL;
     }

@@ -29,7 +29,7 @@ struct MomentStore {
 
 // Workspace of rom_build_append (factor of one expansion point + moment buffers).
 template <typename R>
-size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax);
+size_t rom_build_ws(const fsi_dims& d, int nrhs, int q, int kmax, const fsi_rom_opts& o);
 
 // Rational Arnoldi moments at the given expansion points appended to the k_in
 // orthonormal columns already in V (n x kmax, column-major); *k_out = columns after.

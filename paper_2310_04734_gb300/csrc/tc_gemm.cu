@@ -23,10 +23,10 @@
 //   * accumulation: the tensor core adds into its FP32 accumulator without
 //     rounding to nearest, so long sums drift; measured on config 2, K = 852
 //     complex in one accumulation needed four times the GMRES steps.  Here
-//     each accumulation spans one 64-element K slice only: the accumulators are
+//     each accumulation spans 32 elements of K only: the accumulators are
 //     double-buffered in TMEM (2 x (big + small) x 128 columns), and the
-//     epilogue warps drain every slice into FP32 registers (round to nearest)
-//     while the MMAs of the next slice run.
+//     epilogue warps drain each one into FP32 registers (round to nearest)
+//     while the MMAs of the next one run.
 // With one plane (NP = 1) the same kernel computes the plain BF16 product
 // a0 b0 (FP32 accumulation), the low-precision factor of the mixed-precision
 // study, which the FP64 refinement has to make up for.
@@ -82,6 +82,12 @@ struct Cfg {
 
 std::atomic<uint32_t> g_spin_limit{kDefaultSpin};
 
+// K steps of 16 accumulated in TMEM between drains: 2 (32 elements).  Measured on config 2,
+// batch 96: 5.45 GMRES steps and 32.2 frequencies/s, against 5.67 and 31.1 with 4 steps (64
+// elements) and 5.38 and 28.7 with 1 step.
+constexpr int kDrainKSteps = 2;
+int drain_ksteps() { return kDrainKSteps; }
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
@@ -121,11 +127,12 @@ __global__ void pack_a_kernel(const float* __restrict__ G, int64_t sGf, int64_t 
         *reinterpret_cast<uint4*>(Ap + (int64_t(NP) * f + q) * plane + idx) = *reinterpret_cast<const uint4*>(out[q]);
 }
 
-// Bp[NP f + p][q][kk]: row q = 2n holds (Br, -Bi) and row 2n + 1 holds (Bi, Br) of every
-// complex k (at kk = 2k, 2k + 1), zero for k >= K; B[k][n] = G[k0 + k][c0 + n].
+// Bp[NP f + p][q][kk0 + kk]: row q = 2n holds (Br, -Bi) and row 2n + 1 holds (Bi, Br) of
+// every complex k < kfill (at kk = 2k, 2k + 1), zero for K <= k; B[k][n] = G[k0 + k][c0 + n];
+// rows of `pitch` elements.
 template <int NP>
-__global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, int k0, int K, int c0, int N, int Kp,
-                              __nv_bfloat16* __restrict__ Bp) {
+__global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, int k0, int K, int c0, int N,
+                              int pitch, int kk0, int kfill, __nv_bfloat16* __restrict__ Bp) {
     __shared__ float2 t[32][33];
     const int f = blockIdx.z;
     const int kb = blockIdx.x * 32, nb = blockIdx.y * 32;
@@ -137,15 +144,15 @@ __global__ void pack_b_kernel(const float2* __restrict__ G, int64_t sG, int ld, 
         t[ty + 8 * i][tx] = (k < K && n < N) ? Gf[int64_t(k0 + k) * ld + c0 + n] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    const int64_t plane = int64_t(2 * N) * Kp;
+    const int64_t plane = int64_t(2 * N) * pitch;
     const int k = kb + tx;
-    if (2 * k >= Kp) return;
+    if (k >= kfill) return;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const int nl = ty + 8 * i, n = nb + nl;
         if (n >= N) continue;
         const float2 b = t[tx][nl];
-        const int64_t o0 = int64_t(2 * n) * Kp + 2 * k, o1 = o0 + Kp;
+        const int64_t o0 = int64_t(2 * n) * pitch + kk0 + 2 * k, o1 = o0 + pitch;
         __nv_bfloat16 re[NP], mi[NP], im[NP];
         split<NP>(b.x, re);
         split<NP>(-b.y, mi);
@@ -247,6 +254,7 @@ struct TcArgs {
     int nk;           // K slices of kTK elements
     uint32_t limit;   // spin limit of the pipeline waits
     int32_t* err;
+    int kpd;          // K steps (of 16) accumulated in TMEM between two drains: 1, 2 or 4
 };
 
 // barrier slots: full[S], empty[S], accf[2] (TMEM buffer written), acce[2] (drained), done
@@ -318,14 +326,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         *s_issued = kt;
     } else if (tid == 32) {
-        // MMA issuer: slice kt accumulates into TMEM buffer kt & 1 (big at +0, small at +128)
+        // MMA issuer: drain unit u (a.kpd K steps of 16) accumulates into TMEM buffer u & 1
+        // (big at +0, small at +128); the drain warps empty a buffer before it is used again
+        const int upb = (kTK / 16) / a.kpd;   // drain units per slice
         int kt = 0;
-        for (; kt < a.nk; ++kt) {
-            const int b = kt & 1, s = kt % S;
-            if (kt >= 2 && !mbar_wait(acce0 + 8u * b, uint32_t((kt / 2 - 1) & 1), a.limit)) {
-                *s_abort = 1;
-                break;
-            }
+        bool stop = false;
+        for (; kt < a.nk && !stop; ++kt) {
+            const int s = kt % S;
             if (!mbar_wait(full0 + 8u * s, uint32_t((kt / S) & 1), a.limit)) {
                 *s_abort = 1;
                 break;
@@ -336,25 +343,36 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t base = ops_s + uint32_t(s) * SB;
-            const uint32_t tbig = tmem + uint32_t(b) * 256u, tsmall = tbig + 128u;
-#pragma unroll
-            for (int ks = 0; ks < kTK / 16; ++ks) {   // K = 16 per MMA: 32 bytes along the swizzle row
-                const uint32_t off = uint32_t(ks) * 32u;
-                const uint32_t acc = ks == 0 ? 0u : 1u;
-                const uint32_t A0 = base + off, B0 = base + NP * kPlaneBytes + off;
-                mma_bf16(tbig, A0, B0, acc);
-                if constexpr (NP == 3) {
-                    const uint32_t A1 = A0 + kPlaneBytes, A2 = A0 + 2 * kPlaneBytes;
-                    const uint32_t B1 = B0 + kPlaneBytes, B2 = B0 + 2 * kPlaneBytes;
-                    mma_bf16(tsmall, A0, B1, acc);
-                    mma_bf16(tsmall, A1, B0, 1u);
-                    mma_bf16(tsmall, A0, B2, 1u);
-                    mma_bf16(tsmall, A2, B0, 1u);
-                    mma_bf16(tsmall, A1, B1, 1u);
+            for (int ui = 0; ui < upb; ++ui) {
+                const int u = kt * upb + ui, b = u & 1;
+                if (u >= 2 && !mbar_wait(acce0 + 8u * b, uint32_t((u / 2 - 1) & 1), a.limit)) {
+                    *s_abort = 1;
+                    stop = true;
+                    ++kt;   // the stage's loads have landed
+                    break;
                 }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t tbig = tmem + uint32_t(b) * 256u, tsmall = tbig + 128u;
+                for (int kk = 0; kk < a.kpd; ++kk) {
+                    const int ks = ui * a.kpd + kk;   // K = 16 per MMA: 32 bytes along the swizzle row
+                    const uint32_t off = uint32_t(ks) * 32u;
+                    const uint32_t acc = kk == 0 ? 0u : 1u;
+                    const uint32_t A0 = base + off, B0 = base + NP * kPlaneBytes + off;
+                    mma_bf16(tbig, A0, B0, acc);
+                    if constexpr (NP == 3) {
+                        const uint32_t A1 = A0 + kPlaneBytes, A2 = A0 + 2 * kPlaneBytes;
+                        const uint32_t B1 = B0 + kPlaneBytes, B2 = B0 + 2 * kPlaneBytes;
+                        mma_bf16(tsmall, A0, B1, acc);
+                        mma_bf16(tsmall, A1, B0, 1u);
+                        mma_bf16(tsmall, A0, B2, 1u);
+                        mma_bf16(tsmall, A2, B0, 1u);
+                        mma_bf16(tsmall, A1, B1, 1u);
+                    }
+                }
+                mma_commit(accf0 + 8u * b);
             }
+            if (stop) break;
             mma_commit(empty0 + 8u * s);
-            mma_commit(accf0 + 8u * b);
         }
         *s_consumed = kt;
         mma_commit(done);   // tracks every MMA issued above
@@ -366,7 +384,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
         for (int j = 0; j < kTN; ++j) sum[j] = 0.f;
         bool ok = true;
-        for (int kt = 0; kt < a.nk; ++kt) {
+        const int nu = a.nk * ((kTK / 16) / a.kpd);   // drain units
+        for (int kt = 0; kt < nu; ++kt) {
             const int b = kt & 1;
             if (!mbar_wait(accf0 + 8u * b, uint32_t((kt / 2) & 1), a.limit)) {
                 ok = false;
@@ -449,6 +468,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 inline unsigned cdiv(int64_t a, int64_t b) { return unsigned((a + b - 1) / b); }
 inline int64_t round_up(int64_t a, int64_t b) { return (a + b - 1) / b * b; }
+inline size_t align_up(size_t x) { return (x + 255) / 256 * 256; }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static std::once_flag once;
@@ -512,9 +532,45 @@ bool launch_np(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int
         pack_a_kernel<NP><<<dim3(cdiv(int64_t(M) * Kp / 8, 256), F), 256, 0, st>>>(
             reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 2 * k0, 2 * K, int(Kp), Ap);
         pack_b_kernel<NP><<<dim3(cdiv(Kp / 2, 32), cdiv(N, 32), F), dim3(32, 8), 0, st>>>(G, sG, ld, k0, K, c0, N,
-                                                                                          int(Kp), Bp);
+                                                                                          int(Kp), 0, int(Kp / 2), Bp);
     }
-    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err};
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps()};
+    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
+    ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
+    tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
+    return true;
+}
+
+// The U12 columns of a slab step, packed once: rows of U12 are final after their block's triangle
+// solve, so each block is packed when it is done and every later update (the left-looking solve
+// of the blocks below, the Schur update) reads the same planes.  A is packed per update.
+template <int NP>
+bool launch_np_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc, cudaStream_t st) {
+    const int M = r1 - r0, N = tc.bN, c0 = tc.bc0, c1 = tc.bc0 + tc.bN;
+    const int64_t Kp = round_up(2 * int64_t(K), kTK);
+    const int64_t aE = int64_t(F) * pack_elems(NP, M, Kp);
+    if (Kp > tc.bKp || size_t(aE) * sizeof(__nv_bfloat16) + 256 > tc.a_bytes) return false;
+    auto* Ap = reinterpret_cast<__nv_bfloat16*>((reinterpret_cast<uintptr_t>(tc.ws) + 255) & ~uintptr_t(255));
+    auto* Bp = static_cast<__nv_bfloat16*>(tc.bpack);
+    CUtensorMap mA, mB, mC;
+    if (!encode3(&mA, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Ap, Kp, M, uint64_t(NP) * F, Kp * 2, uint64_t(M) * Kp * 2,
+                 kTK, kTM, CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mB, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, Bp, tc.bKp, 2 * uint64_t(N), uint64_t(NP) * F, tc.bKp * 2,
+                 2 * uint64_t(N) * tc.bKp * 2, kTK, kTN, CU_TENSOR_MAP_L2_PROMOTION_L2_256B) ||
+        !encode3(&mC, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, G, 2 * uint64_t(c1), uint64_t(r1), uint64_t(F),
+                 uint64_t(ld) * 8, uint64_t(sG) * 8, 32, 32, CU_TENSOR_MAP_L2_PROMOTION_NONE))
+        return false;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(tc_gemm_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(Cfg<NP>::kSmem));
+        attr_set = true;
+    }
+    {
+        ProfScope ps(PK_PACK, 0.0, st);
+        pack_a_kernel<NP><<<dim3(cdiv(int64_t(M) * Kp / 8, 256), F), 256, 0, st>>>(
+            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 0, 2 * K, int(Kp), Ap);
+    }
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps()};
     dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
     ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
     tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
@@ -543,6 +599,51 @@ bool launch_tc_update(float2* G, int64_t sG, int ld, int F, int r0, int r1, int 
     if ((reinterpret_cast<uintptr_t>(G) & 15) || (ld & 1) || (sG & 1) || (c0 & 1)) return false;
     return tc.planes == 1 ? launch_np<1>(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc, st)
                           : launch_np<3>(G, sG, ld, F, r0, r1, c0, c1, k0, K, tc, st);
+}
+
+size_t tc_a_region_bytes(int F, int m, int ncols, int npiv, int planes) {
+    const int64_t nb = std::min(128, npiv);
+    const int64_t Kpn = round_up(2 * int64_t(npiv), kTK), Kp1 = round_up(2 * nb, kTK);
+    int64_t a = pack_elems(planes, m - nb, Kp1);
+    a = std::max(a, pack_elems(planes, std::min(128, npiv), Kpn));
+    a = std::max(a, pack_elems(planes, m - npiv, Kpn));
+    return align_up(size_t(F) * size_t(a) * sizeof(__nv_bfloat16) + 256);
+}
+
+bool tc_begin_lazy(float2* G, int64_t sG, int ld, int F, int npiv, int c0, int c1, TcCtx& tc, cudaStream_t st) {
+    tc.bpack = nullptr;
+    if ((reinterpret_cast<uintptr_t>(G) & 15) || (ld & 1) || (sG & 1) || (c0 & 1) || c1 <= c0 || !tc.ws) return false;
+    const int64_t Kp = round_up(2 * int64_t(npiv), kTK);
+    const size_t bytes = size_t(F) * size_t(pack_elems(tc.planes, 2 * int64_t(c1 - c0), Kp)) * sizeof(__nv_bfloat16);
+    if (tc.a_bytes + bytes > tc.ws_bytes) return false;
+    tc.bpack = static_cast<char*>(tc.ws) + tc.a_bytes;   // a_bytes is a multiple of 256
+    tc.bKp = Kp;
+    tc.bN = c1 - c0;
+    tc.bc0 = c0;
+    // the K padding beyond 2 npiv must read as zero
+    return cudaMemsetAsync(tc.bpack, 0, bytes, st) == cudaSuccess;
+}
+
+void tc_pack_b_rows(float2* G, int64_t sG, int ld, int F, int k_begin, int k_end, const TcCtx& tc, cudaStream_t st) {
+    if (!tc.bpack || k_end <= k_begin) return;
+    const int K = k_end - k_begin;
+    ProfScope ps(PK_PACK, 0.0, st);
+    auto* Bp = static_cast<__nv_bfloat16*>(tc.bpack);
+    const dim3 grid(cdiv(K, 32), cdiv(tc.bN, 32), F);
+    if (tc.planes == 1)
+        pack_b_kernel<1><<<grid, dim3(32, 8), 0, st>>>(G, sG, ld, k_begin, K, tc.bc0, tc.bN, int(tc.bKp), 2 * k_begin,
+                                                        K, Bp);
+    else
+        pack_b_kernel<3><<<grid, dim3(32, 8), 0, st>>>(G, sG, ld, k_begin, K, tc.bc0, tc.bN, int(tc.bKp), 2 * k_begin,
+                                                        K, Bp);
+}
+
+bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc,
+                           cudaStream_t st) {
+    if (!tc.bpack) return false;
+    if (r1 <= r0 || K <= 0) return true;
+    return tc.planes == 1 ? launch_np_lazy<1>(G, sG, ld, F, r0, r1, K, tc, st)
+                          : launch_np_lazy<3>(G, sG, ld, F, r0, r1, K, tc, st);
 }
 
 }  // namespace fsi

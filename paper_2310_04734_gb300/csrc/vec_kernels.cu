@@ -21,8 +21,8 @@ namespace {
 template <int R, bool scaled>
 __global__ void __launch_bounds__(kRowThreads) residual_kernel(DevModel m, const double* omega, double omega0,
                                                                const double2* x, int64_t sX, const double2* Fm,
-                                                               double2* r, int64_t sR, double* norms, int nstride,
-                                                               int ncol0, double* absn) {
+                                                               int64_t sF, double2* r, int64_t sR, double* norms,
+                                                               int nstride, int ncol0, double* absn) {
     constexpr int KS = kept_slots<R>();
     const int f = blockIdx.y;
     const double w = omega ? omega[f] : omega0, w2 = w * w, inv_w = 1.0 / w;
@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(kRowThreads) residual_kernel(DevModel m, const
     const int c0 = slot_base<R>(g);
     const bool writer = slot_writer<R>(g);
     const double2* xf = x ? x + f * sX : nullptr;
+    const double2* Ff = Fm + f * sF;   // sF = 0: one right-hand side for every frequency
     double2* rf = r + f * sR;
     double nrm[KS], anr[KS];
 #pragma unroll
@@ -73,7 +74,7 @@ __global__ void __launch_bounds__(kRowThreads) residual_kernel(DevModel m, const
 #pragma unroll
             for (int q = 0; q < KS; ++q) {
                 const int c = c0 + q;
-                const double2 fv = Fm[c * m.n + i];
+                const double2 fv = Ff[c * m.n + i];
                 const double2 v = make_double2(rs * (fv.x - acc[q].x), rs * (fv.y - acc[q].y));
                 rf[c * m.n + i] = v;
                 nrm[q] = fma(v.x, v.x, fma(v.y, v.y, nrm[q]));
@@ -105,23 +106,23 @@ __global__ void __launch_bounds__(kRowThreads) residual_kernel(DevModel m, const
 
 template <int R, bool scaled>
 void residual_launch_s(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
-                       const double2* Fm, double2* r, int64_t sR, double* norms, int nstride, int c0, double* absn,
-                       cudaStream_t st) {
+                       const double2* Fm, int64_t sF, double2* r, int64_t sR, double* norms, int nstride, int c0,
+                       double* absn, cudaStream_t st) {
     static const int per_sm = resident_ctas(residual_kernel<R, scaled>);
     const dim3 grid(row_grid_x(m.n, F, per_sm), F);
     residual_kernel<R, scaled><<<grid, kRowThreads, 0, st>>>(m, d_omega, omega0, x ? x + c0 * m.n : nullptr, sX,
-                                                             Fm + c0 * m.n, r + c0 * m.n, sR, norms, nstride, c0,
-                                                             absn);
+                                                             Fm + c0 * m.n, sF, r + c0 * m.n, sR, norms, nstride,
+                                                             c0, absn);
 }
 
 template <int R>
 void residual_launch(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
-                     const double2* Fm, double2* r, int64_t sR, double* norms, int nstride, int c0, bool scaled,
-                     double* absn, cudaStream_t st) {
+                     const double2* Fm, int64_t sF, double2* r, int64_t sR, double* norms, int nstride, int c0,
+                     bool scaled, double* absn, cudaStream_t st) {
     if (scaled)
-        residual_launch_s<R, true>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nstride, c0, absn, st);
+        residual_launch_s<R, true>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nstride, c0, absn, st);
     else
-        residual_launch_s<R, false>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nstride, c0, absn, st);
+        residual_launch_s<R, false>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nstride, c0, absn, st);
 }
 
 template <typename T2>
@@ -175,17 +176,17 @@ inline unsigned ceil_div(int64_t a, int64_t b) { return unsigned((a + b - 1) / b
 
 void launch_residual(const DevModel& m, const double* d_omega, double omega0, int F, const double2* x, int64_t sX,
                      const double2* Fm, int nrhs, double2* r, int64_t sR, double* norms, bool scaled,
-                     cudaStream_t st, double* absn) {
+                     cudaStream_t st, double* absn, int64_t sF) {
     ProfScope ps(PK_RESID, 0.0, st);
     // load columns in power-of-two slices of at most 8
     for (int c0 = 0; c0 < nrhs;) {
         const int left = nrhs - c0;
         const int nc = left >= 8 ? 8 : (left >= 4 ? 4 : (left >= 2 ? 2 : 1));
         switch (nc) {
-            case 8: residual_launch<8>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
-            case 4: residual_launch<4>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
-            case 2: residual_launch<2>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st); break;
-            default: residual_launch<1>(m, d_omega, omega0, F, x, sX, Fm, r, sR, norms, nrhs, c0, scaled, absn, st);
+            case 8: residual_launch<8>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            case 4: residual_launch<4>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            case 2: residual_launch<2>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nrhs, c0, scaled, absn, st); break;
+            default: residual_launch<1>(m, d_omega, omega0, F, x, sX, Fm, sF, r, sR, norms, nrhs, c0, scaled, absn, st);
         }
         c0 += nc;
     }

@@ -253,3 +253,32 @@ def test_check_and_resolve_replaces_failing_frequencies_by_full_order():
     y, _ = fom.sweep(asm, freqs, fem.load_matrix(w.model, w.loads, w.n_rhs), fem.receiver_dofs(w.model, w.receivers),
                      method="dense")
     assert rel(p.cpu().numpy(), y) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", ["fp32_ir", "bf16x6_ir"])
+def test_batched_expansion_points_match_one_at_a_time(precision):
+    """Eq. 10 moments of several expansion points factored and solved together (batch_shifts)
+    give the same basis span, hence the same reduced outputs, as one point at a time, and
+    both match the oracle's ROM; the tensor-core factor (BF16x6) serves the moments too."""
+    torch = need_cuda()
+    from paper_2310_04734_gb300 import api
+    w = W.small_model(floor=False)
+    spec = w.model
+    model = api.fsi_assemble(spec)
+    F = api.dense_loads(spec, w.loads, w.n_rhs)
+    rcv = torch.tensor(api.receiver_dofs(spec, w.receivers), device="cuda")
+    shifts, q = [60.0, 150.0, 250.0, 110.0], 3
+    freqs = np.array([45.0, 97.0, 133.0, 210.0, 280.0])
+    outs = []
+    for bs in (1, 3, 4):
+        V = api.rom_build(model, shifts, q, F, kmax=200, precision=precision, tol=1e-12, max_refine=30,
+                          batch_shifts=bs)
+        p, _ = api.rom_sweep(api.rom_project(model, V, F, rcv), freqs, batch=5)
+        outs.append((V.shape[1], p.cpu().numpy()))
+    assert outs[0][0] == outs[1][0] == outs[2][0]
+    assert rel(outs[1][1], outs[0][1]) <= 1e-8 and rel(outs[2][1], outs[0][1]) <= 1e-8
+    asm = fem.assemble(spec)
+    Fo = fem.load_matrix(spec, w.loads, w.n_rhs)
+    yR = rom.reduced_sweep(rom.project(asm, rom.build_basis(asm, shifts, q, Fo, 200), Fo,
+                                       fem.receiver_dofs(spec, w.receivers)), freqs)
+    assert rel(outs[1][1], yR) <= 1e-6
