@@ -452,6 +452,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=96)
+    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length of the refinement")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="bf16x6_ir", choices=["fp32_ir", "bf16x6_ir", "bf16_ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -517,11 +518,13 @@ def main():
         return freqs[batch_indices(len(freqs), B, world, rank, step)]
 
     # one workspace serves the device-buffer steps and the host-buffer (e2e) steps
-    ws_bytes = max(api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers)),
-                   api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers), host_io=True))
+    ws_bytes = max(api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers), restart=args.restart),
+                   api.frf_sweep_workspace(model, args.precision, B, w.n_rhs, len(w.receivers), host_io=True,
+                                           restart=args.restart))
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    kw = dict(precision=args.precision, batch=B, max_refine=160, tol=REFINE_TOL, workspace=ws, allow_noconv=True)
+    kw = dict(precision=args.precision, batch=B, max_refine=160, tol=REFINE_TOL, workspace=ws, allow_noconv=True,
+              restart=args.restart)
     for s in range(args.warmup):
         api.frf_sweep_full(model, batch_freqs(s), F, rcv, **kw)
     torch.cuda.synchronize()

@@ -149,10 +149,11 @@ size_t tc_a_region_bytes(int F, int m, int ncols, int npiv, int planes);
 // Columns [c0, c1) right of the npiv pivots: prepare the packed U12 operand (false: the tensor-core
 // path does not apply; use launch_tc_update / the SIMT update).  Then tc_pack_b_rows packs rows
 // [k_begin, k_end) of U12 once they are final, and launch_tc_update_lazy runs
-// C[r0:r1, c0:c1] -= A[r0:r1, 0:K] U12[0:K, c0:c1] from the packed rows.
+// C[r0:r1, c0:c1] -= A[r0:r1, k0:k0+K] U12[k0:k0+K, c0:c1] from the packed rows (2 k0 a multiple
+// of 64; false: not launched).
 bool tc_begin_lazy(float2* G, int64_t sG, int ld, int F, int npiv, int c0, int c1, TcCtx& tc, cudaStream_t st);
 void tc_pack_b_rows(float2* G, int64_t sG, int ld, int F, int k_begin, int k_end, const TcCtx& tc, cudaStream_t st);
-bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc,
+bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int k0, int K, const TcCtx& tc,
                            cudaStream_t st);
 // Spin limit of the tensor-core kernels' pipeline waits (0: the default, about 6.7e7 polls).
 void set_tc_spin_limit(uint32_t spins);

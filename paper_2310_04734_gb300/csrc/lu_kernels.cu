@@ -444,17 +444,8 @@ static int outer_nb() {
 // triangles cost less than that saves (measured on config 2: 18.6 vs 18.3 frequencies/s; 16 rows: 18.2)
 constexpr int kTrsmMaxRows = 32;
 
-// U12 = L11^-1 A12 for the nb pivot rows [J, J+nb): triangles of at most kTrsmMaxRows rows,
-// the rows below each updated by a GEMM with the rows just solved.
-template <typename R>
-void blocked_trsm(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int J, int nb, int c0, int c1,
-                  cudaStream_t st) {
-    for (int r = 0; r < nb; r += kTrsmMaxRows) {
-        const int cnt = std::min(kTrsmMaxRows, nb - r);
-        launch_trsm<R>(G, sG, ld, F, J + r, cnt, c0, c1, st);
-        if (r + cnt < nb) launch_gemm_update<R>(G, sG, ld, F, J + r + cnt, J + nb, c0, c1, J + r, cnt, st);
-    }
-}
+// narrowest update (complex columns) sent to the tensor cores
+constexpr int kTcMinCols = 64;
 
 template <typename R>
 void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int j0, int nbw, int32_t* ipiv,
@@ -524,7 +515,8 @@ template <typename R>
 void trailing_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int c1, int k0, int K,
                      const TcCtx* tc, cudaStream_t st) {
     if constexpr (sizeof(R) == 4) {
-        if (tc && launch_tc_update(G, sG, ld, F, r0, r1, c0, c1, k0, K, *tc, st)) return;
+        // narrow updates (fewer than 64 complex columns) would waste most of a 128-wide tensor tile
+        if (tc && c1 - c0 >= kTcMinCols && launch_tc_update(G, sG, ld, F, r0, r1, c0, c1, k0, K, *tc, st)) return;
     }
     launch_gemm_update<R>(G, sG, ld, F, r0, r1, c0, c1, k0, K, st);
 }
@@ -539,7 +531,11 @@ constexpr int kLazyTrsmRows = 128;
 // first takes the product of the multipliers and all rows above it, K up to npiv) and the
 // Schur complement A22 -= L21 U12 is one update with K = npiv.  The arithmetic is that of the
 // right-looking order (the same pivots; sums in a different order), but most of it runs in
-// updates with a long K.
+// updates with a long K.  With tensor cores the outer-panel updates (K = 128) and every update of
+// the lazy phase run there; the rows of U12 are packed for them once, 32 rows at a time as they
+// are solved, and every later update reads them from there.  The short updates inside an outer
+// panel (K = 16 and 32), which build the diagonal block's own factors, stay on the FP32 pipe
+// (on the tensor cores as well: 1.5 % faster on config 2, no fewer GMRES steps).
 template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv, int32_t* ipiv,
                 int64_t sP, int32_t* status, cudaStream_t st, const TcCtx* tc) {
@@ -558,12 +554,16 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
         }
         launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);
         if (J + nb < npiv) {
-            blocked_trsm<R>(G, sG, ld, F, J, nb, J + nb, npiv, st);
+            for (int r = 0; r < nb; r += kTrsmMaxRows) {   // the outer panel's U rows, 32-row triangles
+                const int cnt = std::min(kTrsmMaxRows, nb - r);
+                launch_trsm<R>(G, sG, ld, F, J + r, cnt, J + nb, npiv, st);
+                if (r + cnt < nb)
+                    launch_gemm_update<R>(G, sG, ld, F, J + r + cnt, J + nb, J + nb, npiv, J + r, cnt, st);
+            }
             trailing_update<R>(G, sG, ld, F, J + nb, m, J + nb, npiv, J, nb, tc, st);
         }
     }
     if (npiv < ncols) {
-        // on the tensor cores the rows of U12 are packed once, block by block as they are solved
         TcCtx lz;
         bool lazy = false;
         if constexpr (sizeof(R) == 4) {
@@ -572,22 +572,27 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
                 lazy = tc_begin_lazy(G, sG, ld, F, npiv, npiv, ncols, lz, st);
             }
         }
-        auto update = [&](int r0, int r1, int K) {
+        // C[r0:r1, npiv:ncols] -= G[r0:r1, k0:k0+K] U12[k0:k0+K, :]
+        auto update = [&](int r0, int r1, int k0, int K) {
             if constexpr (sizeof(R) == 4) {
-                if (lazy && launch_tc_update_lazy(G, sG, ld, F, r0, r1, K, lz, st)) return;
+                if (lazy && launch_tc_update_lazy(G, sG, ld, F, r0, r1, k0, K, lz, st)) return;
                 lazy = false;   // the packed rows are not kept up to date from here on
             }
-            trailing_update<R>(G, sG, ld, F, r0, r1, npiv, ncols, 0, K, tc, st);
+            trailing_update<R>(G, sG, ld, F, r0, r1, npiv, ncols, k0, K, tc, st);
         };
         for (int I = 0; I < npiv; I += kLazyTrsmRows) {
             const int tb = std::min(kLazyTrsmRows, npiv - I);
-            if (I > 0) update(I, I + tb, I);
-            blocked_trsm<R>(G, sG, ld, F, I, tb, npiv, ncols, st);
-            if constexpr (sizeof(R) == 4) {
-                if (lazy) tc_pack_b_rows(G, sG, ld, F, I, I + tb, lz, st);
+            if (I > 0) update(I, I + tb, 0, I);
+            for (int r = 0; r < tb; r += kTrsmMaxRows) {   // 32-row triangles joined by updates
+                const int cnt = std::min(kTrsmMaxRows, tb - r);
+                launch_trsm<R>(G, sG, ld, F, I + r, cnt, npiv, ncols, st);
+                if constexpr (sizeof(R) == 4) {
+                    if (lazy) tc_pack_b_rows(G, sG, ld, F, I + r, I + r + cnt, lz, st);
+                }
+                if (r + cnt < tb) update(I + r + cnt, I + tb, I + r, cnt);
             }
         }
-        if (npiv < m) update(npiv, m, npiv);
+        if (npiv < m) update(npiv, m, 0, npiv);
     }
 }
 

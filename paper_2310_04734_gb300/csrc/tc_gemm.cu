@@ -73,11 +73,13 @@ constexpr int kPlaneBytes = 128 * 128;   // one 128-row plane of a slice (A and 
 constexpr uint32_t kDefaultSpin = 1u << 26;
 constexpr uint32_t kDrainSpin = 1u << 26;   // waits for work already issued (always completes)
 
+constexpr int kStagingBytes = 4 * 2 * 4096;   // output staging: 4 drain warps x 2 buffers
+
 template <int NP>
 struct Cfg {
     static constexpr int kStageBytes = 2 * NP * kPlaneBytes;          // NP planes of A and of B
     static constexpr int kStages = NP == 3 ? 2 : 4;
-    static constexpr size_t kSmem = size_t(kStages) * kStageBytes + 1024 + 256;
+    static constexpr size_t kSmem = size_t(kStages) * kStageBytes + kStagingBytes + 1024 + 256;
 };
 
 std::atomic<uint32_t> g_spin_limit{kDefaultSpin};
@@ -255,8 +257,13 @@ struct TcArgs {
     uint32_t limit;   // spin limit of the pipeline waits
     int32_t* err;
     int kpd;          // K steps (of 16) accumulated in TMEM between two drains: 1, 2 or 4
+    int tiles_x, tiles_y, ntiles;   // 128 x 128 tiles of C per matrix, and over the batch
+    int bx0;          // first K element of the B planes (their rows may hold more of K)
 };
 
+// Persistent: CTA c takes tiles c, c + gridDim.x, ... (x fastest, then y, then the batch member);
+// the slice counter g and the drain-unit counter u run on across tiles, so the loads and MMAs of
+// the next tile overlap the last drains and the output of the previous one.
 // barrier slots: full[S], empty[S], accf[2] (TMEM buffer written), acce[2] (drained), done
 template <int NP>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -269,7 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char* ops = smem_raw + pad;
     const uint32_t ops_s = raw + pad;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + size_t(S) * SB);
+    const uint32_t stage_out = ops_s + uint32_t(S) * SB;   // 4 drain warps x 2 x 4 KiB of output staging
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ops + size_t(S) * SB + kStagingBytes);
     constexpr int kBars = 2 * S + 5;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kBars);
     volatile int* s_abort = reinterpret_cast<volatile int*>(tmem_slot + 1);
@@ -277,9 +285,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* s_consumed = s_abort + 2;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int bx = blockIdx.x, by = blockIdx.y, f = blockIdx.z;
     const uint32_t full0 = smem_u32(&bars[0]), empty0 = smem_u32(&bars[S]), accf0 = smem_u32(&bars[2 * S]),
                    acce0 = smem_u32(&bars[2 * S + 2]), done = smem_u32(&bars[2 * S + 4]);
+    const int per_tile = a.tiles_x * a.tiles_y;
+    const int upb = (kTK / 16) / a.kpd;   // drain units per slice
 
     if (tid == 0) {
         *s_abort = 0;
@@ -306,127 +315,141 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (tid == 0) {
         // TMA producer: NP planes of A, then NP planes of B, per slice
-        int kt = 0;
-        for (; kt < a.nk; ++kt) {
-            const int s = kt % S;
-            if (kt >= S && !mbar_wait(empty0 + 8u * s, uint32_t((kt / S - 1) & 1), a.limit)) {
-                *s_abort = 1;
-                break;
-            }
-            if (*s_abort) break;
-            const uint32_t base = ops_s + uint32_t(s) * SB;
-            const uint32_t fb = full0 + 8u * s;
-            expect_tx(fb, SB);
-            const int x = kt * kTK;
+        int g = 0;
+        bool stop = false;
+        for (int t = blockIdx.x; t < a.ntiles && !stop; t += gridDim.x) {
+            const int f = t / per_tile, rem = t - f * per_tile, by = rem / a.tiles_x, bx = rem - by * a.tiles_x;
+            for (int kt = 0; kt < a.nk; ++kt, ++g) {
+                const int s = g % S;
+                if (g >= S && !mbar_wait(empty0 + 8u * s, uint32_t((g / S - 1) & 1), a.limit)) {
+                    *s_abort = 1;
+                    stop = true;
+                    break;
+                }
+                if (*s_abort) {
+                    stop = true;
+                    break;
+                }
+                const uint32_t base = ops_s + uint32_t(s) * SB;
+                const uint32_t fb = full0 + 8u * s;
+                expect_tx(fb, SB);
+                const int x = kt * kTK;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                tma_load3(base + q * kPlaneBytes, &tmA, x, by * kTM, NP * f + q, fb);
-                tma_load3(base + (NP + q) * kPlaneBytes, &tmB, x, bx * kTN, NP * f + q, fb);
+                for (int q = 0; q < NP; ++q) {
+                    tma_load3(base + q * kPlaneBytes, &tmA, x, by * kTM, NP * f + q, fb);
+                    tma_load3(base + (NP + q) * kPlaneBytes, &tmB, a.bx0 + x, bx * kTN, NP * f + q, fb);
+                }
             }
         }
-        *s_issued = kt;
+        *s_issued = g;
     } else if (tid == 32) {
         // MMA issuer: drain unit u (a.kpd K steps of 16) accumulates into TMEM buffer u & 1
         // (big at +0, small at +128); the drain warps empty a buffer before it is used again
-        const int upb = (kTK / 16) / a.kpd;   // drain units per slice
-        int kt = 0;
+        int g = 0, u = 0;
         bool stop = false;
-        for (; kt < a.nk && !stop; ++kt) {
-            const int s = kt % S;
-            if (!mbar_wait(full0 + 8u * s, uint32_t((kt / S) & 1), a.limit)) {
-                *s_abort = 1;
-                break;
-            }
-            if (*s_abort) {
-                ++kt;   // this stage's loads have landed: nothing left in flight for it
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            const uint32_t base = ops_s + uint32_t(s) * SB;
-            for (int ui = 0; ui < upb; ++ui) {
-                const int u = kt * upb + ui, b = u & 1;
-                if (u >= 2 && !mbar_wait(acce0 + 8u * b, uint32_t((u / 2 - 1) & 1), a.limit)) {
+        for (int t = blockIdx.x; t < a.ntiles && !stop; t += gridDim.x) {
+            for (int kt = 0; kt < a.nk && !stop; ++kt) {
+                const int s = g % S;
+                if (!mbar_wait(full0 + 8u * s, uint32_t((g / S) & 1), a.limit)) {
                     *s_abort = 1;
                     stop = true;
-                    ++kt;   // the stage's loads have landed
+                    break;
+                }
+                ++g;   // this stage's loads have landed
+                if (*s_abort) {
+                    stop = true;
                     break;
                 }
                 asm volatile("tcgen05.fence::after_thread_sync;");
-                const uint32_t tbig = tmem + uint32_t(b) * 256u, tsmall = tbig + 128u;
-                for (int kk = 0; kk < a.kpd; ++kk) {
-                    const int ks = ui * a.kpd + kk;   // K = 16 per MMA: 32 bytes along the swizzle row
-                    const uint32_t off = uint32_t(ks) * 32u;
-                    const uint32_t acc = kk == 0 ? 0u : 1u;
-                    const uint32_t A0 = base + off, B0 = base + NP * kPlaneBytes + off;
-                    mma_bf16(tbig, A0, B0, acc);
-                    if constexpr (NP == 3) {
-                        const uint32_t A1 = A0 + kPlaneBytes, A2 = A0 + 2 * kPlaneBytes;
-                        const uint32_t B1 = B0 + kPlaneBytes, B2 = B0 + 2 * kPlaneBytes;
-                        mma_bf16(tsmall, A0, B1, acc);
-                        mma_bf16(tsmall, A1, B0, 1u);
-                        mma_bf16(tsmall, A0, B2, 1u);
-                        mma_bf16(tsmall, A2, B0, 1u);
-                        mma_bf16(tsmall, A1, B1, 1u);
+                const uint32_t base = ops_s + uint32_t(s) * SB;
+                for (int ui = 0; ui < upb; ++ui, ++u) {
+                    const int b = u & 1;
+                    if (u >= 2 && !mbar_wait(acce0 + 8u * b, uint32_t((u / 2 - 1) & 1), a.limit)) {
+                        *s_abort = 1;
+                        stop = true;
+                        break;
                     }
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                    const uint32_t tbig = tmem + uint32_t(b) * 256u, tsmall = tbig + 128u;
+                    for (int kk = 0; kk < a.kpd; ++kk) {
+                        const int ks = ui * a.kpd + kk;   // K = 16 per MMA: 32 bytes along the swizzle row
+                        const uint32_t off = uint32_t(ks) * 32u;
+                        const uint32_t acc = kk == 0 ? 0u : 1u;
+                        const uint32_t A0 = base + off, B0 = base + NP * kPlaneBytes + off;
+                        mma_bf16(tbig, A0, B0, acc);
+                        if constexpr (NP == 3) {
+                            const uint32_t A1 = A0 + kPlaneBytes, A2 = A0 + 2 * kPlaneBytes;
+                            const uint32_t B1 = B0 + kPlaneBytes, B2 = B0 + 2 * kPlaneBytes;
+                            mma_bf16(tsmall, A0, B1, acc);
+                            mma_bf16(tsmall, A1, B0, 1u);
+                            mma_bf16(tsmall, A0, B2, 1u);
+                            mma_bf16(tsmall, A2, B0, 1u);
+                            mma_bf16(tsmall, A1, B1, 1u);
+                        }
+                    }
+                    mma_commit(accf0 + 8u * b);
                 }
-                mma_commit(accf0 + 8u * b);
+                if (stop) break;
+                mma_commit(empty0 + 8u * s);
             }
-            if (stop) break;
-            mma_commit(empty0 + 8u * s);
         }
-        *s_consumed = kt;
+        *s_consumed = g;
         mma_commit(done);   // tracks every MMA issued above
     } else if (warp >= 4) {
         // drain warps: warp w reads TMEM lanes 32 (w % 4) .. + 31 = tile rows, all 128 columns
         const int q = warp & 3;
         const uint32_t trow = tmem + (uint32_t(32 * q) << 16);
-        float sum[kTN];
-#pragma unroll
-        for (int j = 0; j < kTN; ++j) sum[j] = 0.f;
+        const uint32_t stage0 = stage_out + uint32_t(warp - 4) * 8192u;
+        const int nu = a.nk * upb;   // drain units per tile
+        int u = 0, outs = 0;
         bool ok = true;
-        const int nu = a.nk * ((kTK / 16) / a.kpd);   // drain units
-        for (int kt = 0; kt < nu; ++kt) {
-            const int b = kt & 1;
-            if (!mbar_wait(accf0 + 8u * b, uint32_t((kt / 2) & 1), a.limit)) {
-                ok = false;
-                *s_abort = 1;
-                break;
-            }
-            if (*s_abort) {
-                ok = false;
-                break;
-            }
-            asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+            const int f = t / per_tile, rem = t - f * per_tile, by = rem / a.tiles_x, bx = rem - by * a.tiles_x;
+            float sum[kTN];
 #pragma unroll
-            for (int j = 0; j < kTN / 32; ++j) {
-                uint32_t v[32];
-                tmem_ld32(trow + uint32_t(b) * 256u + uint32_t(32 * j), v);
-                if constexpr (NP == 3) {
-                    uint32_t u[32];
-                    tmem_ld32(trow + uint32_t(b) * 256u + 128u + uint32_t(32 * j), u);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]) + __uint_as_float(u[i]);
-                } else {
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-                    for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]);
+            for (int j = 0; j < kTN; ++j) sum[j] = 0.f;
+            for (int uu = 0; uu < nu; ++uu, ++u) {
+                const int b = u & 1;
+                if (!mbar_wait(accf0 + 8u * b, uint32_t((u / 2) & 1), a.limit)) {
+                    ok = false;
+                    *s_abort = 1;
+                    break;
                 }
+                if (*s_abort) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+                for (int j = 0; j < kTN / 32; ++j) {
+                    uint32_t v[32];
+                    tmem_ld32(trow + uint32_t(b) * 256u + uint32_t(32 * j), v);
+                    if constexpr (NP == 3) {
+                        uint32_t w2[32];
+                        tmem_ld32(trow + uint32_t(b) * 256u + 128u + uint32_t(32 * j), w2);
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]) + __uint_as_float(w2[i]);
+                    } else {
+                        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                        for (int i = 0; i < 32; ++i) sum[32 * j + i] += __uint_as_float(v[i]);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acce0 + 8u * b);
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(acce0 + 8u * b);
-        }
-        if (ok) {
-            // all MMAs have completed (every slice was drained): the operand ring is idle
-            const uint32_t stage0 = ops_s + uint32_t(warp - 4) * 8192u;
+            if (!ok) break;
+            // -sum into C through the dedicated staging buffers (alternating; a buffer is written
+            // again only after the reduce two commits back has read it)
             const int y = a.cy0 + by * kTM + 32 * q;
             const int nch = y < a.cy1 ? min(kTN / 32, (a.cx1 - a.cx0 - bx * kTN + 31) / 32) : 0;
 #pragma unroll
             for (int ch = 0; ch < kTN / 32; ++ch) {
                 if (ch >= nch) break;
-                const uint32_t stg = stage0 + uint32_t(ch & 1) * 4096u;
-                if (ch >= 2) {
+                const uint32_t stg = stage0 + uint32_t(outs & 1) * 4096u;
+                if (outs >= 2) {
                     if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
                     __syncwarp();
                 }
@@ -445,17 +468,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     asm volatile("cp.async.bulk.commit_group;" ::: "memory");
                 }
                 __syncwarp();
+                ++outs;
             }
-            if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-            __syncwarp();
         }
+        if (lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+        __syncwarp();
     }
     __syncthreads();
     // drain: loads and MMAs already issued finish before shared or tensor memory is released
     if (tid == 0) {
         bool ok = true;
-        for (int kt = *s_consumed; kt < *s_issued; ++kt)
-            ok = mbar_wait(full0 + 8u * (kt % S), uint32_t((kt / S) & 1), kDrainSpin) && ok;
+        for (int g = *s_consumed; g < *s_issued; ++g)
+            ok = mbar_wait(full0 + 8u * (g % S), uint32_t((g / S) & 1), kDrainSpin) && ok;
         if (!ok || *s_abort) atomicExch(a.err, 1);
     }
     if (tid == 32 && !mbar_wait(done, 0u, kDrainSpin)) atomicExch(a.err, 1);
@@ -484,6 +508,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
             cudaGetLastError();
     });
     return fn;
+}
+
+int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
+    return n;
+}
+
+// one persistent CTA per SM (the shared memory allows one), at most one per tile
+template <int NP>
+void launch_gemm_kernel(const CUtensorMap& mA, const CUtensorMap& mB, const CUtensorMap& mC, TcArgs args, int M,
+                        int N, int F, cudaStream_t st) {
+    args.tiles_x = int(cdiv(2 * int64_t(N), kTN));
+    args.tiles_y = int(cdiv(M, kTM));
+    args.ntiles = args.tiles_x * args.tiles_y * F;
+    const int grid = std::min(args.ntiles, sm_count());
+    tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
 }
 
 // 3-D tensor map: inner dimension d0 (contiguous), rows d1 (stride s1 bytes), planes d2 (stride s2).
@@ -534,10 +579,9 @@ bool launch_np(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int
         pack_b_kernel<NP><<<dim3(cdiv(Kp / 2, 32), cdiv(N, 32), F), dim3(32, 8), 0, st>>>(G, sG, ld, k0, K, c0, N,
                                                                                           int(Kp), 0, int(Kp / 2), Bp);
     }
-    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps()};
-    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps(), 0, 0, 0, 0};
     ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
-    tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
+    launch_gemm_kernel<NP>(mA, mB, mC, args, M, N, F, st);
     return true;
 }
 
@@ -545,11 +589,14 @@ bool launch_np(float2* G, int64_t sG, int ld, int F, int r0, int r1, int c0, int
 // solve, so each block is packed when it is done and every later update (the left-looking solve
 // of the blocks below, the Schur update) reads the same planes.  A is packed per update.
 template <int NP>
-bool launch_np_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc, cudaStream_t st) {
+bool launch_np_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int k0, int K, const TcCtx& tc,
+                    cudaStream_t st) {
     const int M = r1 - r0, N = tc.bN, c0 = tc.bc0, c1 = tc.bc0 + tc.bN;
     const int64_t Kp = round_up(2 * int64_t(K), kTK);
     const int64_t aE = int64_t(F) * pack_elems(NP, M, Kp);
-    if (Kp > tc.bKp || size_t(aE) * sizeof(__nv_bfloat16) + 256 > tc.a_bytes) return false;
+    // the packed rows start at K element 2 k0, which the slices must meet on their 64-element grid
+    if ((2 * k0) % kTK || 2 * k0 + Kp > tc.bKp || size_t(aE) * sizeof(__nv_bfloat16) + 256 > tc.a_bytes)
+        return false;
     auto* Ap = reinterpret_cast<__nv_bfloat16*>((reinterpret_cast<uintptr_t>(tc.ws) + 255) & ~uintptr_t(255));
     auto* Bp = static_cast<__nv_bfloat16*>(tc.bpack);
     CUtensorMap mA, mB, mC;
@@ -568,12 +615,12 @@ bool launch_np_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K,
     {
         ProfScope ps(PK_PACK, 0.0, st);
         pack_a_kernel<NP><<<dim3(cdiv(int64_t(M) * Kp / 8, 256), F), 256, 0, st>>>(
-            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 0, 2 * K, int(Kp), Ap);
+            reinterpret_cast<const float*>(G), 2 * sG, 2 * int64_t(ld), r0, M, 2 * k0, 2 * K, int(Kp), Ap);
     }
-    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps()};
-    dim3 grid(cdiv(2 * int64_t(N), kTN), cdiv(M, kTM), F);
+    TcArgs args{2 * c0, 2 * c1, r0, r1, int(Kp / kTK), g_spin_limit.load(), tc.err, drain_ksteps(), 0, 0, 0,
+                2 * k0};
     ProfScope ps(PK_TCGEMM, 8.0 * F * double(M) * double(N) * K, st);
-    tc_gemm_kernel<NP><<<grid, kThreads, Cfg<NP>::kSmem, st>>>(mA, mB, mC, args);
+    launch_gemm_kernel<NP>(mA, mB, mC, args, M, N, F, st);
     return true;
 }
 
@@ -638,12 +685,12 @@ void tc_pack_b_rows(float2* G, int64_t sG, int ld, int F, int k_begin, int k_end
                                                         K, Bp);
 }
 
-bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int K, const TcCtx& tc,
+bool launch_tc_update_lazy(float2* G, int64_t sG, int ld, int F, int r0, int r1, int k0, int K, const TcCtx& tc,
                            cudaStream_t st) {
     if (!tc.bpack) return false;
     if (r1 <= r0 || K <= 0) return true;
-    return tc.planes == 1 ? launch_np_lazy<1>(G, sG, ld, F, r0, r1, K, tc, st)
-                          : launch_np_lazy<3>(G, sG, ld, F, r0, r1, K, tc, st);
+    return tc.planes == 1 ? launch_np_lazy<1>(G, sG, ld, F, r0, r1, k0, K, tc, st)
+                          : launch_np_lazy<3>(G, sG, ld, F, r0, r1, k0, K, tc, st);
 }
 
 }  // namespace fsi

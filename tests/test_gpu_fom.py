@@ -168,7 +168,8 @@ def test_cfg2_full_size_sampled_frequencies(precision):
     # cond ~ 5e7 at 20 Hz: a 1e-10 residual keeps the forward error far inside 0.1 dB.  There
     # the FP64 residual of any solution stalls near 2e-10 (the rounding floor of evaluating it),
     # which the refinement accepts as converged.
-    res = api.frf_sweep_full(model, freqs, F, rcv, precision=precision, batch=3, max_refine=80, tol=1e-10)
+    # at 20 Hz the tensor-core factor needs about 100 GMRES steps (the FP32 one about 40)
+    res = api.frf_sweep_full(model, freqs, F, rcv, precision=precision, batch=3, max_refine=160, tol=1e-10)
     print("cfg2 iterations", res.iters.tolist(), "relres", res.relres.tolist())
     # (at 20 Hz the accepted rounding floor of the scaled residual is ~1e-9)
     assert res.stats.n_unconverged == 0 and res.relres.max() <= 5e-9
