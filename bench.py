@@ -452,7 +452,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=96)
-    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length of the refinement")
+    ap.add_argument("--restart", type=int, default=40, help="GMRES restart length of the refinement")
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--precision", default="bf16x6_ir", choices=["fp32_ir", "bf16x6_ir", "bf16_ir", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -677,8 +677,8 @@ def main():
                 "roofline": roofline, "kernels": shares, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clk, "fp64_full_order": fp64,
                 "refine_iters": {"max": int(max(iters)), "mean": float(np.mean(iters)), "unconverged": unconv,
-                                 "method": "GMRES(20) on the FP64 system, preconditioned by the band LU (%s)"
-                                           % args.precision},
+                                 "method": "GMRES(%d) on the FP64 system, preconditioned by the band LU (%s)"
+                                           % (args.restart, args.precision)},
                 "peaks_source": src}
         print(json.dumps(line), flush=True)
     if pg:
