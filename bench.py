@@ -176,7 +176,7 @@ def run_peaks(args):
     from paper_2310_04734_gb300 import api
     clocks = ClockSampler(0)
     clocks.start()
-    probes = measure_peaks(api, seconds=1.0)
+    probes = measure_peaks(api, kinds=tuple(api.PEAK_KINDS), seconds=1.0)
     clk = clocks.stop()
     peaks, src = _peaks()
     print(json.dumps({"mode": "peaks", "tflops": probes, "sm_count": _sm_count(torch), "clocks": clk,

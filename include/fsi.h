@@ -564,7 +564,8 @@ fsi_status mlp_predict(const float* params, const float* X, int n, float* y, voi
  * independent operations and no memory traffic, about seconds_hint seconds,
  * timed with CUDA events on `stream`.  kind 0: FP32 FMA (SIMT), 1: FP64 FMA,
  * 2: tcgen05 MMA with BF16 operands, 3: tcgen05 MMA with TF32 operands
- * (M = 128, N = 256, FP32 accumulation).  scratch: device, >= 1 KiB.  Writes
+ * (M = 128, N = 256, FP32 accumulation), 4: BF16 with M = N = 128 (the
+ * tile of the tensor-core LU updates).  scratch: device, >= 1 KiB.  Writes
  * the achieved TFLOP/s (2 flops per multiply-add) and the kernel time in ms.
  * Synchronizes the stream.  Errors: FSI_EINVAL, FSI_ECUDA, FSI_ETIMEOUT. */
 fsi_status fsi_probe_peak(int kind, double seconds_hint, void* scratch, double* tflops_out, double* ms_out,

@@ -228,7 +228,7 @@ def fsi_set_wait_limit(spins: int = 0):
     L.check(L.load().fsi_set_wait_limit(int(spins)), "fsi_set_wait_limit")
 
 
-PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "bf16_tcgen05": 2, "tf32_tcgen05": 3}
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "bf16_tcgen05": 2, "tf32_tcgen05": 3, "bf16_tcgen05_n128": 4}
 
 
 def fsi_probe_peak(kind: str, seconds: float = 0.2):

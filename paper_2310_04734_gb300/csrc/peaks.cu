@@ -64,10 +64,11 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
     return false;
 }
 
-// One CTA per SM: M = 128, N = 256 MMAs back to back on shared-memory operands (contents
+// One CTA per SM: M = 128, N = NN MMAs back to back on shared-memory operands (contents
 // irrelevant), accumulating into TMEM; every 64 MMAs a commit and a wait bound the queue.
-// KIND 0: kind::f16 with BF16 operands (K = 16 per MMA); 1: kind::tf32 (K = 8).
-template <int KIND>
+// KIND 0: kind::f16 with BF16 operands (K = 16 per MMA); 1: kind::tf32 (K = 8).  NN = 128 is the
+// tile of the band LU's update kernel; NN = 256 is the widest single-CTA shape.
+template <int KIND, int NN>
 __global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t groups, int32_t* err) {
     __shared__ __align__(1024) unsigned char ops[256 * 128];   // A: first 128 rows, B: all 256
     __shared__ uint64_t bar;
@@ -91,7 +92,7 @@ __global__ void __launch_bounds__(128, 1) mma_probe_kernel(int64_t groups, int32
     if (tid == 0) {
         const uint64_t ad = make_desc(smem_u32(ops)), bd = make_desc(smem_u32(ops));
         constexpr uint32_t fmt = KIND == 0 ? 1u : 2u;   // BF16 (kind::f16) or TF32
-        constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(256 >> 3) << 17) |
+        constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | (uint32_t(NN >> 3) << 17) |
                                    (uint32_t(128 >> 4) << 24);
         uint32_t phase = 0;
         for (int64_t g = 0; g < groups; ++g) {
@@ -134,7 +135,7 @@ using namespace fsi;
 
 extern "C" fsi_status fsi_probe_peak(int kind, double seconds_hint, void* scratch, double* tflops_out,
                                      double* ms_out, void* stream) {
-    if (!(tflops_out && scratch && kind >= 0 && kind <= 3)) {
+    if (!(tflops_out && scratch && kind >= 0 && kind <= 4)) {
         set_error("fsi_probe_peak: bad arguments");
         return FSI_EINVAL;
     }
@@ -163,15 +164,18 @@ extern "C" fsi_status fsi_probe_peak(int kind, double seconds_hint, void* scratc
                                                                  static_cast<double*>(scratch));
                 break;
             case 2:
-                mma_probe_kernel<0><<<sms, 128, 0, st>>>(units, static_cast<int32_t*>(scratch));
+                mma_probe_kernel<0, 256><<<sms, 128, 0, st>>>(units, static_cast<int32_t*>(scratch));
+                break;
+            case 3:
+                mma_probe_kernel<1, 256><<<sms, 128, 0, st>>>(units, static_cast<int32_t*>(scratch));
                 break;
             default:
-                mma_probe_kernel<1><<<sms, 128, 0, st>>>(units, static_cast<int32_t*>(scratch));
+                mma_probe_kernel<0, 128><<<sms, 128, 0, st>>>(units, static_cast<int32_t*>(scratch));
                 break;
         }
     };
     if (kind <= 1) flops_per_unit = 2.0 * kChains * kUnroll * 256.0 * sms * 8;
-    else flops_per_unit = 64.0 * 2.0 * 128.0 * 256.0 * (kind == 2 ? 16.0 : 8.0) * sms;
+    else flops_per_unit = 64.0 * 2.0 * 128.0 * (kind == 4 ? 128.0 : 256.0) * (kind == 3 ? 8.0 : 16.0) * sms;
     // calibrate: grow the work until one launch takes about `hint` seconds
     int64_t units = kind <= 1 ? 256 : 16;
     float ms = 0.f;

@@ -205,6 +205,9 @@ def test_invalid_arguments_are_rejected_before_device_work(lib):
     need = C.c_size_t(0)
     assert lib.fsi_lu_workspace(7, 1, 4, 4, 4, C.byref(need)) == -1 and "precision" in last()
     assert lib.fsi_set_wait_limit(-1) == -1
+    tf = C.c_double(0.0)
+    assert lib.fsi_probe_peak(5, 0.1, p, C.byref(tf), None, None) == -1 and "bad arguments" in last()
+    assert lib.fsi_probe_peak(2, 0.1, None, C.byref(tf), None, None) == -1
     assert lib.rom_residual_check(C.byref(dims), p, p, 4, p, p, p, p, p, 9, dp, 1, 1, p, 1 << 20, dp, None) == -1
     assert lib.rom_sweep(4, p, p, p, p, p, 1, 1, dp, 0, 1, 0, p, 1 << 20, p, None, None, None) == -1
     assert lib.rom_sweep(4, p, p, p, p, p, 1, 1, dp, 1, 1, 5, p, 1 << 20, p, None, None, None) == -1 \

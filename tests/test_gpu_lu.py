@@ -115,3 +115,17 @@ def test_tensor_core_wait_timeout_is_reported_and_the_next_call_is_clean():
     R = At.cpu().numpy().astype(np.complex128)
     piv = ipiv.cpu().numpy()
     assert max(_lu_residual(A[i], R[i], piv[i], npiv) for i in range(2)) <= 2e-5 * np.sqrt(m)
+
+
+def test_throughput_probes_report_plausible_rates():
+    """The roofline denominators: every probe returns a positive rate below twice the nominal
+    dense peak of its unit (FP32 80, FP64 1.25, BF16 2250, TF32 1125 TFLOP/s), and the 128 x 128
+    BF16 shape of the LU updates does not exceed the 128 x 256 one by more than timing noise."""
+    need_cuda()
+    from paper_2310_04734_gb300 import api
+    nominal = {"fp32_fma": 80.0, "fp64_fma": 1.25, "bf16_tcgen05": 2250.0, "tf32_tcgen05": 1125.0,
+               "bf16_tcgen05_n128": 2250.0}
+    got = {k: api.fsi_probe_peak(k, 0.05)[0] for k in api.PEAK_KINDS}
+    for k, v in got.items():
+        assert 0.0 < v < 2.0 * nominal[k], (k, v)
+    assert got["bf16_tcgen05_n128"] <= 1.1 * got["bf16_tcgen05"]
