@@ -112,10 +112,11 @@ void launch_form_rows(const DevModel& m, typename Cplx<R>::T* G, int64_t sG, int
                       const double* d_omega, int row_slab, int g_row0, int col_slab0, int wcols,
                       cudaStream_t st);
 
-// Unblocked LU with partial pivoting of the panel rows [j0, m) x cols [j0, j0+nbw).
+// Unblocked LU with partial pivoting of the panel rows [j0, m) x cols [j0, j0+nbw); its row
+// interchanges are applied to the columns [c0, j0) and [j0+nbw, c1) as well.
 template <typename R>
 void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int j0, int nbw,
-                  int32_t* ipiv, int64_t sP, int32_t* status, cudaStream_t st);
+                  int32_t* ipiv, int64_t sP, int32_t* status, int c0, int c1, cudaStream_t st);
 // Row interchanges ipiv[j..j+cnt) on columns [a0,a1) and [b0,b1).
 template <typename R>
 void launch_laswp(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int j, int cnt, const int32_t* ipiv,

@@ -22,7 +22,7 @@ namespace fsi {
 namespace {
 
 constexpr int kPanelThreads = 1024;
-constexpr size_t kMaxPanelSmem = 220 * 1024;
+constexpr size_t kMaxPanelSmem = 226 * 1024;
 
 template <typename T2>
 struct Real;
@@ -63,126 +63,221 @@ __global__ void form_rows_kernel(DevModel m, T2* G, int64_t sG, int ld, const do
 }
 
 // ----------------------------------------------------------------- panel LU
-template <typename T2>
-__device__ void block_argmax(typename Real<T2>::R& val, int& idx, typename Real<T2>::R* sv, int* si) {
-    using R = typename Real<T2>::R;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int off = 16; off > 0; off >>= 1) {
-        R ov = __shfl_down_sync(0xffffffffu, val, off);
-        int oi = __shfl_down_sync(0xffffffffu, idx, off);
-        if (ov > val || (ov == val && oi < idx)) {
-            val = ov;
-            idx = oi;
-        }
+// (v, k, r): a candidate pivot's |.|^2, its logical row and its physical row in shared memory;
+// the larger v wins, ties go to the smaller logical row (the first maximum, as in LAPACK)
+template <typename R>
+__device__ __forceinline__ void amax_merge(R& v, int& k, int& r, R ov, int ok, int orow) {
+    if (ov > v || (ov == v && ok < k)) {
+        v = ov;
+        k = ok;
+        r = orow;
     }
-    if (lane == 0) {
-        sv[warp] = val;
-        si[warp] = idx;
-    }
-    __syncthreads();
-    if (warp == 0) {
-        const int nw = blockDim.x >> 5;
-        val = lane < nw ? sv[lane] : R(-1);
-        idx = lane < nw ? si[lane] : 0x7fffffff;
-        for (int off = 16; off > 0; off >>= 1) {
-            R ov = __shfl_down_sync(0xffffffffu, val, off);
-            int oi = __shfl_down_sync(0xffffffffu, idx, off);
-            if (ov > val || (ov == val && oi < idx)) {
-                val = ov;
-                idx = oi;
-            }
-        }
-        if (lane == 0) {
-            sv[32] = val;
-            si[32] = idx;
-        }
-    }
-    __syncthreads();
-    val = sv[32];
-    idx = si[32];
 }
 
-// Panel rows [j0, m) x columns [j0, j0+nbw), column-major copy P[t * mr + i] in shared memory.
+// butterfly: every lane ends with the warp's maximum
+template <typename R>
+__device__ __forceinline__ void warp_amax(R& v, int& k, int& r) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const R ov = __shfl_xor_sync(0xffffffffu, v, off);
+        const int ok = __shfl_xor_sync(0xffffffffu, k, off);
+        const int orow = __shfl_xor_sync(0xffffffffu, r, off);
+        amax_merge(v, k, r, ov, ok, orow);
+    }
+}
+
+constexpr int kPanelHdr = 2048;   // warp maxima (two slots), moved-row list and its count
+
+// LU with partial pivoting of the panel rows [j0, m) x columns [j0, j0 + nbw), held in shared
+// memory (column-major, P[t * ms + i] for physical row i).  Rows are not moved while the panel
+// is factored: pos[i] is the logical position of physical row i, and the interchange of step t
+// (logical rows t and q, q the pivot's position) only exchanges two entries of pos.  The rows
+// still below the pivots (pos >= t) take their multipliers and rank-1 updates in place, and the
+// same pass forms the argmax of column t + 1, so one barrier separates two steps.  The panel is
+// written back in logical order, ipiv holds LAPACK's sequence of interchanges, and the rows that
+// moved are moved in the columns [c0, j0) and [j0 + nbw, c1) as well (the rest of the outer panel).
 template <typename T2>
 __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG, int ld, int m, int j0, int nbw,
-                                                              int32_t* ipiv, int64_t sP, int32_t* status) {
+                                                              int32_t* ipiv, int64_t sP, int32_t* status, int c0,
+                                                              int c1) {
     using R = typename Real<T2>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    R* sv = reinterpret_cast<R*>(smem_raw);
-    int* si = reinterpret_cast<int*>(smem_raw + 64 * sizeof(double));
-    T2* P = reinterpret_cast<T2*>(smem_raw + 64 * sizeof(double) + 64 * sizeof(int));
+    R* pv = reinterpret_cast<R*>(smem_raw);                            // [2][32]
+    int* pk = reinterpret_cast<int*>(smem_raw + 64 * sizeof(double));  // [2][32] logical rows
+    int* pr = pk + 64;                                                 // [2][32] physical rows
+    int* nmoved = pr + 64;
+    int* moved = nmoved + 4;                                           // physical rows whose pos changed
+    const int mr = m - j0;
+    int* pos = reinterpret_cast<int*>(smem_raw + kPanelHdr);
+    T2* P = reinterpret_cast<T2*>(smem_raw + kPanelHdr + ((size_t(mr) * 4 + 15) & ~size_t(15)));
     const int f = blockIdx.x;
     T2* A = G + f * sG;
-    const int mr = m - j0;
-    const int ms = mr | 1;   // odd column stride: the 8/16-byte row-wise stores hit distinct banks
-    for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
+    const int ms = mr | 1;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int idx = tid; idx < mr * nbw; idx += blockDim.x) {
         const int i = idx / nbw, t = idx - i * nbw;
         P[t * ms + i] = A[int64_t(j0 + i) * ld + j0 + t];
     }
+    for (int i = tid; i < mr; i += blockDim.x) pos[i] = i;
+    if (tid == 0) *nmoved = 0;
     __syncthreads();
+    R bv = R(-1);
+    int bk = 0x7fffffff, br = -1;
+    for (int i = tid; i < mr; i += blockDim.x) {
+        const T2 v = P[i];
+        amax_merge(bv, bk, br, v.x * v.x + v.y * v.y, i, i);
+    }
     for (int t = 0; t < nbw; ++t) {
-        R best = R(-1);
-        int bi = 0x7fffffff;
-        for (int i = t + threadIdx.x; i < mr; i += blockDim.x) {
-            const T2 v = P[t * ms + i];
-            const R a = v.x * v.x + v.y * v.y;
-            if (a > best || (a == best && i < bi)) {
-                best = a;
-                bi = i;
-            }
+        warp_amax(bv, bk, br);
+        const int slot = (t & 1) * 32;
+        if (lane == 0) {
+            pv[slot + warp] = bv;
+            pk[slot + warp] = bk;
+            pr[slot + warp] = br;
         }
-        block_argmax<T2>(best, bi, sv, si);
-        const bool bad = !(best > R(0)) || isinf(best) || bi >= mr;
+        __syncthreads();
+        bv = lane < nw ? pv[slot + lane] : R(-1);
+        bk = lane < nw ? pk[slot + lane] : 0x7fffffff;
+        br = lane < nw ? pr[slot + lane] : -1;
+        warp_amax(bv, bk, br);
+        const int q = bk, p = br;
+        const bool bad = !(bv > R(0)) || isinf(bv) || p < 0;
+        R nv = R(-1);
+        int nk = 0x7fffffff, nr = -1;   // argmax of column t + 1 over the rows left below
+        const bool next = t + 1 < nbw;
         if (bad) {
-            if (threadIdx.x == 0) {
+            // no usable pivot: the row at position t stays there and the column is left as it is
+            if (tid == 0) {
                 status[f] = 1;
                 ipiv[f * sP + j0 + t] = j0 + t;
             }
-            __syncthreads();
-            continue;  // leave the column as is; the factor is singular
-        }
-        if (threadIdx.x == 0) ipiv[f * sP + j0 + t] = j0 + bi;
-        if (bi != t) {
-            for (int u = threadIdx.x; u < nbw; u += blockDim.x) {
-                const T2 x = P[u * ms + t];
-                P[u * ms + t] = P[u * ms + bi];
-                P[u * ms + bi] = x;
+            for (int i = tid; i < mr && next; i += blockDim.x) {
+                const int ps = pos[i];
+                if (ps <= t) continue;
+                const T2 v = P[(t + 1) * ms + i];
+                amax_merge(nv, nk, nr, v.x * v.x + v.y * v.y, ps, i);
+            }
+        } else {
+            const T2 inv = cinv(P[t * ms + p]);
+            if (tid == 0) ipiv[f * sP + j0 + t] = j0 + q;
+            for (int i = tid; i < mr; i += blockDim.x) {
+                int ps = pos[i];
+                if (i == p) {
+                    pos[i] = t;
+                    continue;
+                }
+                if (ps < t) continue;   // a pivot row of an earlier step
+                if (ps == t) {          // displaced by the interchange
+                    ps = q;
+                    pos[i] = q;
+                }
+                const T2 l = cmul(P[t * ms + i], inv);
+                P[t * ms + i] = l;
+                for (int u = t + 1; u < nbw; ++u) cfms(P[u * ms + i], l, P[u * ms + p]);
+                if (next) {
+                    const T2 v = P[(t + 1) * ms + i];
+                    amax_merge(nv, nk, nr, v.x * v.x + v.y * v.y, ps, i);
+                }
             }
         }
-        __syncthreads();
-        const T2 inv = cinv(P[t * ms + t]);
-        for (int i = t + 1 + threadIdx.x; i < mr; i += blockDim.x) {
-            const T2 l = cmul(P[t * ms + i], inv);
-            P[t * ms + i] = l;
-            for (int u = t + 1; u < nbw; ++u) cfms(P[u * ms + i], l, P[u * ms + t]);
+        bv = nv;
+        bk = nk;
+        br = nr;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < mr * nbw; idx += blockDim.x) {
+        const int i = idx / nbw, t = idx - i * nbw;
+        A[int64_t(j0 + pos[i]) * ld + j0 + t] = P[t * ms + i];
+    }
+    for (int i = tid; i < mr; i += blockDim.x)
+        if (pos[i] != i) moved[atomicAdd(nmoved, 1)] = i;
+    // the same interchanges in the other columns of the outer panel, staged through shared memory
+    // nbw columns at a time (the moved rows are at most mr, so a chunk fits in the panel's space)
+    const int nleft = j0 - c0, nother = nleft + max(c1 - j0 - nbw, 0);
+    __syncthreads();
+    const int nm = *nmoved;
+    for (int cb = 0; cb < nother && nm > 0; cb += nbw) {
+        const int w = min(nbw, nother - cb);
+        for (int e = tid; e < nm * w; e += blockDim.x) {
+            const int k = e / w, c = cb + e - k * w;
+            const int col = c < nleft ? c0 + c : j0 + nbw + (c - nleft);
+            P[e] = A[int64_t(j0 + moved[k]) * ld + col];
         }
         __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < mr * nbw; idx += blockDim.x) {
-        const int i = idx / nbw, t = idx - i * nbw;
-        A[int64_t(j0 + i) * ld + j0 + t] = P[t * ms + i];
+        for (int e = tid; e < nm * w; e += blockDim.x) {
+            const int k = e / w, c = cb + e - k * w;
+            const int col = c < nleft ? c0 + c : j0 + nbw + (c - nleft);
+            A[int64_t(j0 + pos[moved[k]]) * ld + col] = P[e];
+        }
+        __syncthreads();
     }
 }
 
 // ----------------------------------------------------------------- laswp
+constexpr int kSwpCols = 32;      // columns per CTA
+constexpr int kSwpThreads = 256;
+
+// Row interchanges ipiv[j .. j + cnt) (LAPACK order) applied to the columns [a0, a1) and [b0, b1).
+// Each CTA forms the composite permutation of the rows involved (every involved row is traced
+// back through the interchanges by one thread), stages its columns of the rows that move in
+// shared memory and writes them to their destinations: two passes of coalesced row segments in
+// place of cnt dependent swaps per column.
 template <typename T2>
-__global__ void laswp_kernel(T2* G, int64_t sG, int ld, int j, int cnt, const int32_t* ipiv, int64_t sP, int a0,
-                             int a1, int b0, int b1) {
-    const int f = blockIdx.y;
-    const int na = a1 > a0 ? a1 - a0 : 0;
-    const int nbc = b1 > b0 ? b1 - b0 : 0;
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= na + nbc) return;
-    const int c = q < na ? a0 + q : b0 + (q - na);
+__global__ void __launch_bounds__(kSwpThreads) laswp_kernel(T2* G, int64_t sG, int ld, int j, int cnt,
+                                                            const int32_t* ipiv, int64_t sP, int a0, int a1, int b0,
+                                                            int b1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    int* piv = reinterpret_cast<int*>(smem_raw);   // [cnt]
+    int* src = piv + cnt;                          // [2 cnt]
+    int* dst = src + 2 * cnt;                      // [2 cnt]
+    int* nmv = dst + 2 * cnt;
+    T2* S = reinterpret_cast<T2*>(smem_raw + ((size_t(5 * cnt + 4) * 4 + 15) & ~size_t(15)));   // [2 cnt][kSwpCols]
+    const int f = blockIdx.y, tid = threadIdx.x;
     T2* A = G + f * sG;
-    const int32_t* piv = ipiv + f * sP;
-    for (int t = 0; t < cnt; ++t) {
-        const int p = piv[j + t];
-        if (p != j + t) {
-            const T2 x = A[int64_t(j + t) * ld + c];
-            A[int64_t(j + t) * ld + c] = A[int64_t(p) * ld + c];
-            A[int64_t(p) * ld + c] = x;
+    for (int t = tid; t < cnt; t += blockDim.x) piv[t] = ipiv[f * sP + j + t];
+    if (tid == 0) *nmv = 0;
+    __syncthreads();
+    // involved rows: j + t for t < cnt, and the first occurrence of each target below the block
+    for (int e = tid; e < 2 * cnt; e += blockDim.x) {
+        int r;
+        if (e < cnt) {
+            r = j + e;
+        } else {
+            const int t = e - cnt;
+            r = piv[t];
+            if (r < j + cnt) continue;
+            bool first = true;
+            for (int u = 0; u < t && first; ++u) first = piv[u] != r;
+            if (!first) continue;
         }
+        int s = r;   // the row whose content ends at r: the interchanges applied in reverse
+        for (int t = cnt - 1; t >= 0; --t) {
+            const int p = piv[t];
+            if (s == j + t) s = p;
+            else if (s == p) s = j + t;
+        }
+        if (s != r) {
+            const int k = atomicAdd(nmv, 1);
+            src[k] = s;
+            dst[k] = r;
+        }
+    }
+    __syncthreads();
+    const int n = *nmv, na = a1 > a0 ? a1 - a0 : 0;
+    const int ntot = na + (b1 > b0 ? b1 - b0 : 0);
+    const int q0 = blockIdx.x * kSwpCols;
+    for (int e = tid; e < n * kSwpCols; e += blockDim.x) {
+        const int k = e / kSwpCols, q = q0 + e - k * kSwpCols;
+        if (q >= ntot) continue;
+        const int col = q < na ? a0 + q : b0 + (q - na);
+        S[e] = A[int64_t(src[k]) * ld + col];
+    }
+    __syncthreads();
+    for (int e = tid; e < n * kSwpCols; e += blockDim.x) {
+        const int k = e / kSwpCols, q = q0 + e - k * kSwpCols;
+        if (q >= ntot) continue;
+        const int col = q < na ? a0 + q : b0 + (q - na);
+        A[int64_t(dst[k]) * ld + col] = S[e];
     }
 }
 
@@ -425,11 +520,16 @@ void launch_form_rows(const DevModel& m, typename Cplx<R>::T* G, int64_t sG, int
     form_rows_kernel<<<grid, 256, 0, st>>>(m, G, sG, ld, d_omega, row_slab, g_row0, col_slab0, wcols);
 }
 
+// shared memory of panel_kernel for m - j0 = mr rows and width w
+template <typename R>
+size_t panel_smem(int mr, int w) {
+    return kPanelHdr + ((size_t(mr) * 4 + 15) & ~size_t(15)) + size_t(mr | 1) * w * sizeof(typename Cplx<R>::T);
+}
+
 template <typename R>
 int panel_width(int m) {
-    const size_t el = sizeof(typename Cplx<R>::T);
     for (int w = 32; w >= 2; w >>= 1)
-        if (size_t(m + 1) * w * el + 64 * (sizeof(double) + sizeof(int)) <= kMaxPanelSmem) return w;
+        if (panel_smem<R>(m, w) <= kMaxPanelSmem) return w;
     return 1;
 }
 
@@ -449,26 +549,33 @@ constexpr int kTcMinCols = 64;
 
 template <typename R>
 void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int j0, int nbw, int32_t* ipiv,
-                  int64_t sP, int32_t* status, cudaStream_t st) {
+                  int64_t sP, int32_t* status, int c0, int c1, cudaStream_t st) {
     using T2 = typename Cplx<R>::T;
-    const size_t smem = 64 * (sizeof(double) + sizeof(int)) + size_t((m - j0) | 1) * nbw * sizeof(T2);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(panel_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem + 2048));
+        cudaFuncSetAttribute(panel_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
         attr_set = true;
     }
     ProfScope ps(PK_PANEL, 0.0, st);
-    panel_kernel<T2><<<F, kPanelThreads, smem, st>>>(G, sG, ld, m, j0, nbw, ipiv, sP, status);
+    panel_kernel<T2><<<F, kPanelThreads, panel_smem<R>(m - j0, nbw), st>>>(G, sG, ld, m, j0, nbw, ipiv, sP, status,
+                                                                           c0, c1);
 }
 
 template <typename R>
 void launch_laswp(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int j, int cnt, const int32_t* ipiv,
                   int64_t sP, int a0, int a1, int b0, int b1, cudaStream_t st) {
+    using T2 = typename Cplx<R>::T;
     const int ncols = (a1 > a0 ? a1 - a0 : 0) + (b1 > b0 ? b1 - b0 : 0);
-    if (ncols <= 0) return;
-    dim3 grid(ceil_div(ncols, 256), F);
+    if (ncols <= 0 || cnt <= 0) return;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(laswp_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    const size_t smem = ((size_t(5 * cnt + 4) * 4 + 15) & ~size_t(15)) + size_t(2 * cnt) * kSwpCols * sizeof(T2);
+    dim3 grid(ceil_div(ncols, kSwpCols), F);
     ProfScope ps(PK_LASWP, 0.0, st);
-    laswp_kernel<<<grid, 256, 0, st>>>(G, sG, ld, j, cnt, ipiv, sP, a0, a1, b0, b1);
+    laswp_kernel<T2><<<grid, kSwpThreads, smem, st>>>(G, sG, ld, j, cnt, ipiv, sP, a0, a1, b0, b1);
 }
 
 template <typename R>
@@ -545,8 +652,7 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
         const int nb = std::min(NB, npiv - J);
         for (int j = J; j < J + nb; j += nbw) {
             const int w = std::min(nbw, J + nb - j);
-            launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, st);
-            launch_laswp<R>(G, sG, ld, F, j, w, ipiv, sP, J, j, j + w, J + nb, st);
+            launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, J, J + nb, st);
             if (j + w < J + nb) {
                 launch_trsm<R>(G, sG, ld, F, j, w, j + w, J + nb, st);
                 launch_gemm_update<R>(G, sG, ld, F, j + w, m, j + w, J + nb, j, w, st);
@@ -627,8 +733,8 @@ void launch_backsub(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int n, in
     template void launch_form_rows<R>(const DevModel&, Cplx<R>::T*, int64_t, int, int, const double*, int, int, int, \
                                       int, cudaStream_t);                                                            \
     template int panel_width<R>(int);                                                                                \
-    template void launch_panel<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*,       \
-                                  cudaStream_t);                                                                     \
+    template void launch_panel<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int32_t*, int64_t, int32_t*, int, \
+                                  int, cudaStream_t);                                                                \
     template void launch_laswp<R>(Cplx<R>::T*, int64_t, int, int, int, int, const int32_t*, int64_t, int, int, int, \
                                   int, cudaStream_t);                                                                \
     template void launch_trsm<R>(Cplx<R>::T*, int64_t, int, int, int, int, int, int, cudaStream_t);                 \
