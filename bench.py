@@ -39,6 +39,10 @@ REFINE_TOL = 1e-10
 METRIC = "FRF frequencies/sec at <=0.1 dB SPL error vs FP64 full-order sweep; tensor-pipe %"
 UNIT = "frequencies/s"
 GEMM_BYTES_PER_FLOP = 465.3e6 / 31.35e9
+# DRAM bytes (read + write) per complex flop (8 M N K) of the tensor-core Schur update, from one
+# ncu capture of 8 config-2 windows (550.7 + 78.3 MB for 8 x 8 x 852 x 1704 x 852 flops); the
+# short-K updates move more bytes per flop, so this scaled figure is a lower bound for them
+TC_BYTES_PER_FLOP = (550.7e6 + 78.3e6) / (8 * 8.0 * 852 * 1704 * 852)
 
 
 def _peaks():
@@ -628,7 +632,9 @@ def main():
                     "frac": (alg_rate / peak) if alg_rate else None,
                     "achieved_executed": exec_rate, "frac_executed": (exec_rate / peak) if exec_rate else None,
                     "tensor_pipe_frac": (exec_rate * nprod / float(peaks["bf16_tflops"])) if exec_rate else None,
-                    "traffic": None,
+                    "traffic": (TC_BYTES_PER_FLOP * kern_flops[g] / max(kern_n[g], 1)) if nprod == 6 else None,
+                    "traffic_unit": "bytes per launch (mean launch; scaled from an ncu capture of the Schur update, "
+                                    "a lower bound for the short-K launches)",
                     "peak_source": f"of measured: bf16 {peaks['bf16_tflops']} TFLOP/s (MEASURED_PEAKS.json) / "
                                    f"{nprod} product(s); probe of this run {probes.get('bf16_tcgen05')}"}
     else:

@@ -213,9 +213,11 @@ fsi_status fsi_batched_lu(int precision, int batch, int m, int ncols, int npiv, 
 /* Spin limit of the bounded mbarrier waits in the tensor-core kernels: the
  * number of polls after which a kernel gives up, records FSI_ETIMEOUT, waits
  * for the loads and MMAs it already issued and releases its tensor memory.
- * 0 restores the default (about 6.7e7 polls, seconds); small values make the
- * waits run out on purpose (tests of the timeout path).  Process-wide, host
- * only.  Errors: FSI_EINVAL (negative). */
+ * Each poll suspends the waiting thread for at most 4 us (it resumes as soon
+ * as the awaited phase completes).  0 restores the default (about 4.2e6
+ * polls, at most ~17 s); small values make the waits run out on purpose
+ * (tests of the timeout path).  Process-wide, host only.  Errors: FSI_EINVAL
+ * (negative). */
 fsi_status fsi_set_wait_limit(int64_t spins);
 
 /* Allocation-free variant of fsi_batched_lu (the paper has no counterpart; it

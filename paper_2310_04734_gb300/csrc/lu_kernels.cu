@@ -96,10 +96,13 @@ constexpr int kPanelHdr = 2048;   // warp maxima (two slots), moved-row list and
 // same pass forms the argmax of column t + 1, so one barrier separates two steps.  The panel is
 // written back in logical order, ipiv holds LAPACK's sequence of interchanges, and the rows that
 // moved are moved in the columns [c0, j0) and [j0 + nbw, c1) as well (the rest of the outer panel).
-template <typename T2>
-__global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG, int ld, int m, int j0, int nbw,
+// NBW > 0 fixes the width at compile time (index arithmetic by shifts, unrolled column loops: the
+// kernel is bound by instruction issue); NBW = 0 takes it from nbw_arg.
+template <typename T2, int NBW>
+__global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG, int ld, int m, int j0, int nbw_arg,
                                                               int32_t* ipiv, int64_t sP, int32_t* status, int c0,
                                                               int c1) {
+    const int nbw = NBW > 0 ? NBW : nbw_arg;
     using R = typename Real<T2>::R;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* pv = reinterpret_cast<R*>(smem_raw);                            // [2][32]
@@ -127,6 +130,9 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG,
         const T2 v = P[i];
         amax_merge(bv, bk, br, v.x * v.x + v.y * v.y, i, i);
     }
+    // with the width fixed at compile time every step is unrolled, so each step's column loop has
+    // its own trip count (no predicated-off columns)
+#pragma unroll(NBW > 0 ? NBW : 1)
     for (int t = 0; t < nbw; ++t) {
         warp_amax(bv, bk, br);
         const int slot = (t & 1) * 32;
@@ -173,7 +179,13 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG,
                 }
                 const T2 l = cmul(P[t * ms + i], inv);
                 P[t * ms + i] = l;
-                for (int u = t + 1; u < nbw; ++u) cfms(P[u * ms + i], l, P[u * ms + p]);
+                if constexpr (NBW > 0) {
+#pragma unroll
+                    for (int u = 1; u < NBW; ++u)
+                        if (u > t) cfms(P[u * ms + i], l, P[u * ms + p]);
+                } else {
+                    for (int u = t + 1; u < nbw; ++u) cfms(P[u * ms + i], l, P[u * ms + p]);
+                }
                 if (next) {
                     const T2 v = P[(t + 1) * ms + i];
                     amax_merge(nv, nk, nr, v.x * v.x + v.y * v.y, ps, i);
@@ -197,15 +209,16 @@ __global__ void __launch_bounds__(kPanelThreads) panel_kernel(T2* G, int64_t sG,
     __syncthreads();
     const int nm = *nmoved;
     for (int cb = 0; cb < nother && nm > 0; cb += nbw) {
-        const int w = min(nbw, nother - cb);
-        for (int e = tid; e < nm * w; e += blockDim.x) {
-            const int k = e / w, c = cb + e - k * w;
+        for (int e = tid; e < nm * nbw; e += blockDim.x) {
+            const int k = e / nbw, c = cb + e - k * nbw;
+            if (c >= nother) continue;
             const int col = c < nleft ? c0 + c : j0 + nbw + (c - nleft);
             P[e] = A[int64_t(j0 + moved[k]) * ld + col];
         }
         __syncthreads();
-        for (int e = tid; e < nm * w; e += blockDim.x) {
-            const int k = e / w, c = cb + e - k * w;
+        for (int e = tid; e < nm * nbw; e += blockDim.x) {
+            const int k = e / nbw, c = cb + e - k * nbw;
+            if (c >= nother) continue;
             const int col = c < nleft ? c0 + c : j0 + nbw + (c - nleft);
             A[int64_t(j0 + pos[moved[k]]) * ld + col] = P[e];
         }
@@ -553,12 +566,17 @@ void launch_panel(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int 
     using T2 = typename Cplx<R>::T;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(panel_kernel<T2>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
+        cudaFuncSetAttribute(panel_kernel<T2, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
+        cudaFuncSetAttribute(panel_kernel<T2, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
+        cudaFuncSetAttribute(panel_kernel<T2, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
+        cudaFuncSetAttribute(panel_kernel<T2, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kMaxPanelSmem));
         attr_set = true;
     }
     ProfScope ps(PK_PANEL, 0.0, st);
-    panel_kernel<T2><<<F, kPanelThreads, panel_smem<R>(m - j0, nbw), st>>>(G, sG, ld, m, j0, nbw, ipiv, sP, status,
-                                                                           c0, c1);
+    const size_t smem = panel_smem<R>(m - j0, nbw);
+    auto kern = nbw == 16 ? panel_kernel<T2, 16>
+                          : nbw == 8 ? panel_kernel<T2, 8> : nbw == 32 ? panel_kernel<T2, 32> : panel_kernel<T2, 0>;
+    kern<<<F, kPanelThreads, smem, st>>>(G, sG, ld, m, j0, nbw, ipiv, sP, status, c0, c1);
 }
 
 template <typename R>
@@ -631,6 +649,37 @@ void trailing_update(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int r0, 
 // rows per block of the left-looking solve U12 = L11^-1 A12 of the columns right of the pivots
 constexpr int kLazyTrsmRows = 128;
 
+// smallest batch whose outer panels are factored recursively (factor_outer_cols).  The recursion
+// moves less of C but solves triangles of up to 64 rows where the flat loop solves 16-row ones;
+// those are latency-bound, so a few matrices are faster with the flat loop (measured on config-2
+// windows: batch 96 22.7 vs 23.0 ms, batch 1 5.2 vs 4.9 ms).
+constexpr int kRecursiveMinBatch = 32;
+
+// Columns [j, j + w) of the outer panel [J, J + nb), factored recursively: the left half (a
+// multiple of the panel width) is factored, its U rows are solved for the right half's columns
+// (32-row triangles joined by updates), the right half takes the update with K = the left
+// half's width, and is factored in turn.  The leaves are panels of at most nbw columns, whose
+// interchanges reach the whole outer panel.  The arithmetic is that of the right-looking order
+// over nbw-column panels; the updates of C inside the outer panel shrink from
+// (nb - nbw) + (nb - 2 nbw) + ... columns of C read and written to nb / 2 per level.
+template <typename R>
+void factor_outer_cols(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int J, int nb, int j, int w,
+                       int nbw, int32_t* ipiv, int64_t sP, int32_t* status, const TcCtx* tc, cudaStream_t st) {
+    if (w <= nbw) {
+        launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, J, J + nb, st);
+        return;
+    }
+    const int h = (w / 2 + nbw - 1) / nbw * nbw;
+    factor_outer_cols<R>(G, sG, ld, F, m, J, nb, j, h, nbw, ipiv, sP, status, tc, st);
+    for (int r = 0; r < h; r += kTrsmMaxRows) {
+        const int cnt = std::min(kTrsmMaxRows, h - r);
+        launch_trsm<R>(G, sG, ld, F, j + r, cnt, j + h, j + w, st);
+        if (r + cnt < h) launch_gemm_update<R>(G, sG, ld, F, j + r + cnt, j + h, j + h, j + w, j + r, cnt, st);
+    }
+    trailing_update<R>(G, sG, ld, F, j + h, m, j + h, j + w, j, h, tc, st);
+    factor_outer_cols<R>(G, sG, ld, F, m, J, nb, j + h, w - h, nbw, ipiv, sP, status, tc, st);
+}
+
 // Partial LU of the first npiv columns, right-looking in outer panels of NB columns, with the
 // updates of the outer panels restricted to the pivot columns [0, npiv).  The columns right of
 // them, [npiv, ncols), only receive their row interchanges while the pivot columns are
@@ -640,9 +689,10 @@ constexpr int kLazyTrsmRows = 128;
 // right-looking order (the same pivots; sums in a different order), but most of it runs in
 // updates with a long K.  With tensor cores the outer-panel updates (K = 128) and every update of
 // the lazy phase run there; the rows of U12 are packed for them once, 32 rows at a time as they
-// are solved, and every later update reads them from there.  The short updates inside an outer
-// panel (K = 16 and 32), which build the diagonal block's own factors, stay on the FP32 pipe
-// (on the tensor cores as well: 1.5 % faster on config 2, no fewer GMRES steps).
+// are solved, and every later update reads them from there.  Inside an outer panel the columns
+// are factored recursively for batches of kRecursiveMinBatch or more (factor_outer_cols; its
+// updates of at least 64 columns go to the tensor cores as well, the narrower ones stay on the
+// FP32 pipe), right-looking over nbw-column panels for smaller batches.
 template <typename R>
 void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int ncols, int npiv, int32_t* ipiv,
                 int64_t sP, int32_t* status, cudaStream_t st, const TcCtx* tc) {
@@ -650,12 +700,16 @@ void partial_lu(typename Cplx<R>::T* G, int64_t sG, int ld, int F, int m, int nc
     const int nbw = std::min(panel_width<R>(m), NB);
     for (int J = 0; J < npiv; J += NB) {
         const int nb = std::min(NB, npiv - J);
-        for (int j = J; j < J + nb; j += nbw) {
-            const int w = std::min(nbw, J + nb - j);
-            launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, J, J + nb, st);
-            if (j + w < J + nb) {
-                launch_trsm<R>(G, sG, ld, F, j, w, j + w, J + nb, st);
-                launch_gemm_update<R>(G, sG, ld, F, j + w, m, j + w, J + nb, j, w, st);
+        if (F >= kRecursiveMinBatch) {
+            factor_outer_cols<R>(G, sG, ld, F, m, J, nb, J, nb, nbw, ipiv, sP, status, tc, st);
+        } else {
+            for (int j = J; j < J + nb; j += nbw) {   // right-looking over nbw-column panels
+                const int w = std::min(nbw, J + nb - j);
+                launch_panel<R>(G, sG, ld, F, m, j, w, ipiv, sP, status, J, J + nb, st);
+                if (j + w < J + nb) {
+                    launch_trsm<R>(G, sG, ld, F, j, w, j + w, J + nb, st);
+                    launch_gemm_update<R>(G, sG, ld, F, j + w, m, j + w, J + nb, j, w, st);
+                }
             }
         }
         launch_laswp<R>(G, sG, ld, F, J, nb, ipiv, sP, 0, J, J + nb, ncols, st);

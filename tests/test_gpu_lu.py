@@ -20,10 +20,13 @@ def _apply_ipiv(A, ipiv):
 @pytest.mark.parametrize("dtype,tol,tc", [("complex128", 1e-12, False), ("complex64", 2e-5, False),
                                            ("complex64", 2e-5, "bf16x6"), ("complex64", 2e-2, "bf16")])
 @pytest.mark.parametrize("batch,m,ncols,npiv", [(3, 70, 70, 70), (2, 200, 300, 100), (4, 333, 401, 131),
-                                                (1, 1, 1, 1), (2, 130, 130, 65), (2, 300, 650, 200)])
+                                                (1, 1, 1, 1), (2, 130, 130, 65), (2, 300, 650, 200),
+                                                (32, 300, 650, 200)])
 def test_batched_partial_lu(dtype, tol, tc, batch, m, ncols, npiv):
     """tc: the long trailing updates run on the tcgen05 tensor cores, with three BF16 planes per
-    operand (FP32 accuracy) or one (plain BF16 products, FP32 accumulation)."""
+    operand (FP32 accuracy) or one (plain BF16 products, FP32 accumulation).  Batches of 32 and
+    more factor each outer panel recursively (outer panels of 128 and a ragged 72 columns here),
+    smaller ones right-looking over panels."""
     torch = need_cuda()
     from paper_2310_04734_gb300 import api
     rng = np.random.default_rng(m * 7 + ncols)
