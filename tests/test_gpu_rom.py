@@ -238,8 +238,12 @@ def test_check_and_resolve_replaces_failing_frequencies_by_full_order():
     rel_l, res_l, n_l = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=loose)
     assert n_l == 0 and not res_l.any() and torch.equal(p, keep_p) and torch.equal(spl, keep_spl)
     assert np.allclose(rel_l, ref, rtol=1e-12, atol=0)
-    # a tolerance between the residuals re-solves exactly the frequencies above it
-    mid = float(np.median(ref.max(axis=1)))
+    # a tolerance between the residuals re-solves exactly the frequencies above it: placed in the
+    # widest relative gap between two of them, since the call recomputes the residuals and norms
+    # reduced with atomics may differ in the last bits from those of rom_residual_check
+    r = np.sort(ref.max(axis=1))
+    g = int(np.argmax(r[1:] / r[:-1]))
+    mid = float(np.sqrt(r[g] * r[g + 1]))
     _, res_m, n_m = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p.clone(), spl.clone(), res_tol=mid)
     assert n_m == int((ref.max(axis=1) > mid).sum()) and (res_m == (ref.max(axis=1) > mid)).all()
     rel_0, res_0, n_0 = api.rom_check_resolve(model, V, rm, F, rcv, freqs, p, spl, res_tol=0.0)
