@@ -40,9 +40,9 @@ METRIC = "FRF frequencies/sec at <=0.1 dB SPL error vs FP64 full-order sweep; te
 UNIT = "frequencies/s"
 GEMM_BYTES_PER_FLOP = 465.3e6 / 31.35e9
 # DRAM bytes (read + write) per complex flop (8 M N K) of the tensor-core Schur update, from one
-# ncu capture of 8 config-2 windows (550.7 + 78.3 MB for 8 x 8 x 852 x 1704 x 852 flops); the
+# ncu capture of 8 config-2 windows (585.4 + 78.3 MB for 8 x 8 x 852 x 1704 x 852 flops); the
 # short-K updates move more bytes per flop, so this scaled figure is a lower bound for them
-TC_BYTES_PER_FLOP = (550.7e6 + 78.3e6) / (8 * 8.0 * 852 * 1704 * 852)
+TC_BYTES_PER_FLOP = (585.4e6 + 78.3e6) / (8 * 8.0 * 852 * 1704 * 852)
 
 
 def _peaks():
