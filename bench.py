@@ -609,8 +609,9 @@ def main():
 
     peaks, src = _peaks()
     b, nz = int(model.dims.b), int(model.dims.nz)
-    # SURVEY 8(d) counts (8/3 + 8) b^3 real flops per slab step of the block LU (the coupling
-    # blocks are sparse); the band LU with pivoting across the stacked panel of two slabs executes
+    # the block LU's algorithmic count is (8/3 + 8) b^3 real flops per slab step (the LU of a b x b
+    # complex block plus one b^3 complex product; the coupling blocks are sparse); the band LU with
+    # pivoting across the stacked panel of two slabs executes
     # sum_j 8 (2b - j)(3b - j) = 8 (6 - 5/2 + 1/3) b^3 = 30.67 b^3, so each launch's executed
     # count is credited with the fraction alg_frac of algorithmic work
     alg_step = (8.0 / 3.0 + 8.0) * b ** 3
@@ -654,7 +655,7 @@ def main():
                     "peak_derived": derived}
     roofline.update({
         "kernel_share_of_profiled": float(kern_ms[g] / max(prof_ms, 1e-9)),
-        "alg_flops_note": "achieved = executed flops x %.4f: SURVEY 8(d) counts 10.67 b^3 per slab step, the band LU "
+        "alg_flops_note": "achieved = executed flops x %.4f: the block LU's algorithmic work is 10.67 b^3 per slab step, the band LU "
                           "executes 30.67 b^3 (pivoting across the stacked panel makes the coupling blocks dense)"
                           % alg_frac,
         "lu_alg_tflops_end_to_end": alg_per_freq * value / 1e12,
